@@ -1,0 +1,174 @@
+/*
+ * gim.h - C ABI of the GB300 IMM library (libgim.so).
+ *
+ * IMM on reverse-reachable (RR) sets, as accelerated by gIM (Shahrouz,
+ * Salehkaleybar, Hashemi, "gIM: GPU Accelerated RIS-based Influence
+ * Maximization Algorithm", IEEE TPDS; arXiv 2009.07325):
+ *   - RR-set sampling under the IC and LT diffusion models (Sec. III-B,
+ *     Alg. 3 and 6; Sec. III-F),
+ *   - greedy maximum coverage over the RR sets (Alg. 1 lines 6-10,
+ *     Sec. III-G, Alg. 7),
+ *   - IMM's lower-bound search and theta in FP64 on the host (Alg. 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a gim_status; none throws, aborts or exits. On an
+ *     error, gim_last_error_string(ctx) describes it.
+ *   - All pointer arguments are HOST pointers unless a name says otherwise.
+ *     Inputs are copied before the call returns; the caller keeps ownership
+ *     of every buffer it passes. Outputs are written into caller-owned
+ *     buffers of the stated length.
+ *   - A context owns all of its device memory and runs its work on one CUDA
+ *     stream of one device. A context must not be used from two threads at
+ *     once; distinct contexts are independent.
+ *   - Vertex ids are uint32 in [0, n); edge counts and RR-set ids are uint64.
+ *   - Randomness: RR set j is a pure function of (graph, model, seed, j).
+ *     It is drawn with Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *     64-bit seed, with counter (idx, tag, j_lo, j_hi): tag 0 draws the root
+ *     (idx 0), tag 1 the IC coin of in-edge e (idx e/4, word e%4), tag 2 the
+ *     LT draw at vertex x (idx x, word 0). Results therefore do not depend
+ *     on thread counts, launch shapes or the order in which RR sets finish.
+ */
+#ifndef GIM_H_
+#define GIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gim_ctx gim_ctx;
+
+/* Diffusion models of Sec. II-B. */
+typedef enum { GIM_IC = 0, GIM_LT = 1 } gim_model;
+
+typedef enum {
+  GIM_OK = 0,
+  GIM_ERR_ARG = 1,      /* an argument is out of range or inconsistent      */
+  GIM_ERR_OOM = 2,      /* device or host memory could not be obtained      */
+  GIM_ERR_CUDA = 3,     /* a CUDA call failed (message has the CUDA error)  */
+  GIM_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up               */
+  GIM_ERR_STATE = 5     /* call not valid in the context's current state    */
+} gim_status;
+
+/*
+ * Creates a context on CUDA device `device` (0-based). If `stream` is not
+ * NULL it must be a cudaStream_t of that device, owned by the caller and
+ * alive for the context's lifetime; all work of the context is issued on
+ * it. With NULL the context creates and owns a non-blocking stream.
+ * *out receives the context. Errors: GIM_ERR_ARG (out NULL, bad device),
+ * GIM_ERR_CUDA, GIM_ERR_OOM.
+ */
+gim_status gim_create(gim_ctx **out, int device, void *stream);
+
+/* Frees every resource of the context. NULL is accepted. */
+void gim_destroy(gim_ctx *ctx);
+
+/*
+ * Loads graph G = (V, E) with n = |V| vertices and m = |E| directed edges as
+ * an in-edge CSR (the CSR of Sec. III-B, indexed by target): the sources u
+ * of the edges u->v are in_sources[in_offsets[v] .. in_offsets[v+1]), in
+ * ascending order without repeats, and in_weights holds p(u,v) of Sec. II-A
+ * for the same positions (fp32, in [0, 1]).
+ *   in_offsets: n+1 entries, in_offsets[0] = 0, non-decreasing, last = m.
+ *   in_sources: m entries, each < n, strictly ascending within a row.
+ *   in_weights: m entries.
+ * Precomputes the IC coin thresholds and the LT cumulative thresholds
+ * (Sec. III-F). The graph is usable under LT only if every row's weights
+ * sum to at most 1 + 1e-6 (Sec. II-B); gim_graph_lt_valid reports it.
+ * Replaces any previous graph and empties the RR collection.
+ * Limits: 2 <= n < 2^32 - 1, m < 2^32 - 4.
+ * Errors: GIM_ERR_ARG (violated layout or range; the context is unchanged),
+ * GIM_ERR_OOM, GIM_ERR_CUDA.
+ */
+gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *in_offsets,
+                          const uint32_t *in_sources, const float *in_weights);
+
+/* *out = 1 if the loaded graph satisfies the LT weight condition, else 0. */
+gim_status gim_graph_lt_valid(gim_ctx *ctx, int *out);
+
+/*
+ * Appends `count` random RR sets with ids |R| .. |R|+count-1 to the
+ * context's collection R (Alg. 1 line 4; Alg. 6), drawn under `model` with
+ * the 64-bit `seed`. IC: the vertices from which the root reaches along
+ * live edges, each in-edge live with its probability (Sec. II-E, Alg. 3).
+ * LT: the walk that, at each vertex, picks at most one in-edge with
+ * probability equal to its weight (Sec. III-F). The occurrence counts
+ * (Occur of Sec. III-B) are updated.
+ * Errors: GIM_ERR_STATE (no graph; or model/seed differ from those of a
+ * non-empty collection: call gim_reset_rr first), GIM_ERR_ARG (LT on a
+ * graph whose weights are not LT-valid), GIM_ERR_OOM, GIM_ERR_CUDA.
+ * On error the collection is left as it was before the call.
+ */
+gim_status gim_sample_rr(gim_ctx *ctx, gim_model model, uint64_t count, uint64_t seed);
+
+/* Empties the RR collection (keeps the graph). */
+gim_status gim_reset_rr(gim_ctx *ctx);
+
+/*
+ * Greedy maximum coverage over the collection (Alg. 1 lines 6-10;
+ * Sec. III-G): k rounds, each taking the vertex outside the seed set that
+ * lies in the most RR sets not yet covered (lowest id on ties), then
+ * removing the RR sets it covers. Once all sets are covered, the remaining
+ * rounds take the lowest unselected ids with gain 0.
+ *   seeds_out:   k entries, the seeds in selection order (required).
+ *   covered_out: nullable; the number of RR sets covered by all k seeds.
+ *   gains_out:   nullable, k entries; the marginal coverage of each seed.
+ * The collection is not modified. Errors: GIM_ERR_ARG (k = 0, k > n, or
+ * seeds_out NULL), GIM_ERR_STATE (no graph), GIM_ERR_OOM, GIM_ERR_CUDA.
+ */
+gim_status gim_select_seeds(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *covered_out,
+                            uint32_t *gains_out);
+
+/*
+ * IMM end to end (Alg. 2 then Alg. 1, with IMM's constants from Tang, Shi
+ * and Xiao, SIGMOD 2015): ell' = ell (1 + ln 2 / ln n), eps' = sqrt(2) eps;
+ * for i = 1 .. floor(log2 n) - 1: x = n / 2^i, sample until
+ * |R| >= ceil(lambda' / x), select k seeds, and stop with
+ * LB = n F_R(S) / (1 + eps') once n F_R(S) >= (1 + eps') x (LB = 1 if
+ * never); then sample until |R| >= theta = ceil(lambda* / LB) and return
+ * the greedy seeds over R. RR sets drawn during the search are reused.
+ * Empties the collection first; leaves the final collection in place.
+ *   seeds_out: k entries (required). theta_out, lb_out: nullable.
+ * Errors: GIM_ERR_ARG (k = 0 or k > n, eps not in (0, 1), ell <= 0,
+ * LT on a graph that is not LT-valid), GIM_ERR_STATE (no graph),
+ * GIM_ERR_OOM, GIM_ERR_CUDA.
+ */
+gim_status gim_imm(gim_ctx *ctx, gim_model model, uint32_t k, double eps, double ell, uint64_t seed,
+                   uint32_t *seeds_out, uint64_t *theta_out, double *lb_out);
+
+/* ---- introspection (tests, tools) ------------------------------------- */
+
+/* *count_out = |R|; *members_out (nullable) = total members over all sets. */
+gim_status gim_rr_count(gim_ctx *ctx, uint64_t *count_out, uint64_t *members_out);
+
+/*
+ * Copies R out in rr_id order as a CSR: offsets_out has |R|+1 entries,
+ * members_out has gim_rr_count's members_out entries; the members of each
+ * set are written in ascending vertex order.
+ */
+gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out);
+
+/* Copies the n occurrence counts (RR sets containing each vertex). */
+gim_status gim_coverage_export(gim_ctx *ctx, uint32_t *cnt_out);
+
+/*
+ * Per-phase device times of the last gim_imm / gim_sample_rr /
+ * gim_select_seeds call, in milliseconds, from CUDA events:
+ * out[0] sampling, out[1] selection (index build + greedy rounds),
+ * out[2] wall time of the call, out[3] lower-bound rounds run by gim_imm.
+ */
+gim_status gim_last_timings(gim_ctx *ctx, double out[4]);
+
+/* Number of kernels this context has launched since it was created. */
+gim_status gim_launch_count(gim_ctx *ctx, uint64_t *out);
+
+/* Human-readable description of the context's last error ("" if none). */
+const char *gim_last_error_string(gim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIM_H_ */

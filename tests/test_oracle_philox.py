@@ -1,0 +1,129 @@
+"""Pins of the oracle's Philox4x32-10 and of the coin / root / LT draws built on it.
+
+The oracle's Philox (Salmon et al., SC'11) is checked against an independent
+implementation of the same generator, triton's ``tl.philox`` run on the CPU by
+triton's interpreter, over random counters and keys. The draws that use it
+are then checked statistically: uniformity of the words, the IC coin rate per
+edge probability, and the uniformity of the root draw.
+"""
+import json
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+_TRITON_SCRIPT = textwrap.dedent(
+    r"""
+    import json, os, sys
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def k(out, c0p, c1p, c2p, c3p, seed, N: tl.constexpr):
+        i = tl.arange(0, N)
+        a, b, c, d = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i))
+        tl.store(out + i * 4 + 0, a)
+        tl.store(out + i * 4 + 1, b)
+        tl.store(out + i * 4 + 2, c)
+        tl.store(out + i * 4 + 3, d)
+
+    req = json.loads(sys.stdin.read())
+    res = []
+    for case in req:
+        N = len(case["ctr"])
+        ctr = np.array(case["ctr"], dtype=np.uint32)
+        cols = [torch.from_numpy(np.ascontiguousarray(ctr[:, q])) for q in range(4)]
+        out = torch.zeros(N * 4, dtype=torch.uint32)
+        k[(1,)](out, *cols, case["seed"], N=N)
+        res.append(out.numpy().reshape(N, 4).astype(np.int64).tolist())
+    print(json.dumps(res))
+    """
+)
+
+
+def test_philox_matches_triton_interpreter(oracle_mod, tmp_path):
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(12345)
+    cases = []
+    for seed in [0, 1, 7, 0xFFFFFFFF, 0x123456789ABCDEF0, (1 << 64) - 1]:
+        ctr = rng.integers(0, 1 << 32, size=(64, 4), dtype=np.uint64).astype(np.uint32)
+        ctr[0] = 0
+        ctr[1] = [0xFFFFFFFF] * 4
+        cases.append({"seed": seed, "ctr": ctr.astype(np.int64).tolist()})
+    script = tmp_path / "tri_philox.py"
+    script.write_text(_TRITON_SCRIPT)
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    p = subprocess.run([sys.executable, str(script)], input=json.dumps(cases), capture_output=True, text=True,
+                       env=env, timeout=600)
+    if p.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {p.stderr[-300:]}")
+    got = json.loads(p.stdout.strip().splitlines()[-1])
+    for case, tri in zip(cases, got):
+        seed = case["seed"]
+        key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+        for ctr, t in zip(case["ctr"], tri):
+            o = oracle_mod.philox4x32_10(np.array(ctr, np.uint32), key)
+            assert o.tolist() == t, (seed, ctr)
+
+
+def test_philox_words_uniform(oracle_mod):
+    """Chi-square on the top 4 bits of 4 * 20000 words (15 dof, far tail cut)."""
+    counts = np.zeros(16, np.int64)
+    key = np.array([7, 0], np.uint32)
+    for i in range(20000):
+        w = oracle_mod.philox4x32_10(np.array([i, 1, 3, 0], np.uint32), key)
+        np.add.at(counts, (w >> 28).astype(np.int64), 1)
+    exp = counts.sum() / 16
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    assert chi2 < 50.0, chi2     # P(chi2_15 > 50) ~ 1e-5
+
+
+@pytest.mark.parametrize("p", [0.0, 1.0 / 16, 0.25, 1.0 / 3, 0.5, 0.9, 1.0])
+def test_ic_coin_rate(oracle_mod, p):
+    """The coin of edge e is live with probability p (5-sigma binomial band)."""
+    N = 40000
+    live = sum(oracle_mod.ic_live(11, j, e, p) for j in range(N // 40) for e in range(40))
+    if p in (0.0, 1.0):
+        assert live == N * p
+        return
+    sd = np.sqrt(N * p * (1 - p))
+    assert abs(live - N * p) < 5 * sd, (live, N * p)
+
+
+def test_ic_coin_edges_independent(oracle_mod):
+    """The four edges sharing one Philox call get different words (no reuse)."""
+    hits = np.zeros((4, 4), np.int64)
+    for j in range(4000):
+        a = [oracle_mod.ic_live(5, j, e, 0.5) for e in range(8, 12)]
+        for x in range(4):
+            for y in range(4):
+                hits[x, y] += a[x] and a[y]
+    off = hits[~np.eye(4, dtype=bool)]
+    # pairs should be live together about 1/4 of the time, not 1/2
+    assert np.all(np.abs(off - 1000) < 5 * np.sqrt(4000 * 0.25 * 0.75)), hits
+
+
+def test_root_uniform(oracle_mod):
+    n = 10
+    N = 50000
+    c = np.bincount([oracle_mod.root(7, j, n) for j in range(N)], minlength=n)
+    chi2 = float(((c - N / n) ** 2 / (N / n)).sum())
+    assert c.size == n and chi2 < 40.0, c
+
+
+def test_root_large_n_in_range(oracle_mod):
+    n = (1 << 32) - 2
+    r = [oracle_mod.root(3, j, n) for j in range(2000)]
+    assert max(r) < n and min(r) >= 0
+    assert np.mean(r) / n == pytest.approx(0.5, abs=0.05)
+
+
+def test_lt_draw_uniform(oracle_mod):
+    N = 40000
+    w = np.array([oracle_mod.lt_draw(9, j, 5) for j in range(N)], np.uint64)
+    c = np.bincount((w >> np.uint64(28)).astype(np.int64), minlength=16)
+    chi2 = float(((c - N / 16) ** 2 / (N / 16)).sum())
+    assert chi2 < 50.0
