@@ -1,0 +1,314 @@
+"""Benchmark: IMM end to end on R-MAT scale 22, IC weighted cascade, k=50, eps=0.1.
+
+One step is one full IMM run through the C ABI (lower-bound search with its
+RR sampling and greedy rounds, then sampling up to theta and the final
+greedy) on a graph resident in HBM. The JSON line reports RR sets per second
+(value), the IMM seconds per run (ms_per_step), an end-to-end figure through
+host buffers (graph upload from pinned memory + IMM + seed readback), the
+roofline position of the dominant kernel (the RR-sampling kernel) against the
+measured HBM copy bandwidth, and the CPU oracle timed on a bounded sample of
+the same workload on this machine's host cores.
+
+Multi-GPU (torchrun, one process per GPU): each rank runs its own
+independent IMM replica (replicas only); value = RR sets over all ranks / the
+slowest rank's time.
+
+--impl reference times the CPU oracle (the only reference implementation this
+method has here) on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IMM end-to-end s & RR-sets/s (IC, R-MAT-22, k=50, ε=0.1); % HBM peak"
+WORKLOAD = dict(workload="imm-ic-wc-rmat22", graph="R-MAT scale 22 (16*2^22 draws, a,b,c,d=.57/.19/.19/.05, "
+                "dedup, seed 3)", weights="weighted cascade 1/indeg(v) fp32", model="IC", k=50, eps=0.1, ell=1.0,
+                philox_seed=7)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def aggregate(units: float, seconds: float):
+    """Whole-job totals over ranks: sum of units, max of seconds."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return units, seconds
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    s = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per unit from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2009_07325_gb300", "csrc", "sample.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == h:
+            return float(parts[2]), parts[3]          # bytes per unit, unit name
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_workload():
+    from paper_2009_07325_gb300 import inputs as I
+    return I.wc_weights(I.rmat(22, 3))
+
+
+def algorithmic_bytes(cnt: np.ndarray, indeg: np.ndarray) -> float:
+    """IC sampling: per member v of an RR set, 8 B of offsets, 8 B per in-edge
+    (source + coin threshold), 4 B store write, 4 B count update."""
+    return float(np.dot(cnt.astype(np.float64), 16.0 + 8.0 * indeg.astype(np.float64)))
+
+
+def cpu_baseline(graph, budget_s: float = 12.0):
+    """The oracle, as it stands, on a bounded sample of the workload on all host cores."""
+    import oracle as O
+    O.build()
+    th = max(1, O.max_threads())
+    o = O.Oracle(graph)
+    t0 = time.perf_counter()
+    chunk = 4000
+    while time.perf_counter() - t0 < budget_s:
+        o.sample(O.IC, WORKLOAD["philox_seed"], chunk, th)
+    o.greedy(WORKLOAD["k"])
+    dt = time.perf_counter() - t0
+    n = o.rr_count
+    return {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle",
+            "sample": f"{n} IC RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g = load_workload()
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(g, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            steps.append(r)
+    units = sum(float(r["sample"].split()[0]) for r in steps)
+    secs = sum(float(r["sample"].split()[0]) / r["value"] for r in steps)
+    value = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RR-sets/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": dict(WORKLOAD, l2="n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": "RR-sets/s", "cores": steps[0]["cores"], "kind": "oracle",
+                             "sample": steps[0]["sample"]},
+            "e2e": {"value": value, "unit": "RR-sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07325_gb300 import GIM_IC, Context
+
+    g = load_workload()
+    indeg = g.indegree()
+    stream = torch.cuda.Stream(device=local)
+    ctx = Context(local, stream=stream.cuda_stream)
+    ctx.load(g)
+    k, eps, ell, seed = WORKLOAD["k"], WORKLOAD["eps"], WORKLOAD["ell"], WORKLOAD["philox_seed"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=f"cuda:{local}")
+
+    for _ in range(args.warmup):
+        ctx.imm(GIM_IC, k, eps, ell, seed)
+
+    ctx.reset_timings()
+    launches0 = ctx.launch_count()
+    step_ms, rr_sets, alg_bytes, sample_ms, select_ms, thetas = [], 0, 0.0, 0.0, 0.0, []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)                       # evict L2 between steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = ctx.imm(GIM_IC, k, eps, ell, seed)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            t = ctx.timings()
+            sample_ms += t["sample_ms"]
+            select_ms += t["select_ms"]
+            rr_sets += r["rr_count"]
+            thetas.append(r["theta"])
+            alg_bytes += algorithmic_bytes(ctx.coverage(), indeg)
+    torch.cuda.synchronize()
+    barrier()
+    tk = ctx.timings()
+    launches = ctx.launch_count() - launches0
+    local_s = sum(step_ms) / 1e3
+    units, secs = aggregate(float(rr_sets), local_s)
+
+    # end to end through host buffers: graph upload from pinned memory, IMM, seeds back
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    off_p, src_p, w_p = pin(g.offsets), pin(g.sources), pin(g.weights)
+    h2d = off_p.nbytes + src_p.nbytes + w_p.nbytes
+    e2e_t, e2e_units = 0.0, 0
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.graph_load(g.n, off_p, src_p, w_p)
+        r = ctx.imm(GIM_IC, k, eps, ell, seed)
+        e2e_t += time.perf_counter() - t0
+        e2e_units += r["rr_count"]
+    e2e_u, e2e_s = aggregate(float(e2e_units), e2e_t)
+    d2h = 4 * k + 8 + 8
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        achieved = alg_bytes / (tk["kernel_ms"] / 1e3) / 1e9 if tk["kernel_ms"] > 0 else 0.0
+        tr = traffic_record("sample_ic_kernel")
+        traffic = None
+        if tr is not None:
+            per_unit, unit = tr
+            traffic = per_unit * (rr_sets / max(tk["kernel_launches"], 1)) if unit == "rr_set" else None
+        line = {
+            "metric": METRIC, "value": units / secs, "unit": "RR-sets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"replicas{world}", l2="flushed between steps (512 MiB write)"),
+            "imm_s": secs / args.steps, "theta": thetas[-1], "rr_sets_per_step": rr_sets / args.steps,
+            "sample_ms_per_step": sample_ms / args.steps, "select_ms_per_step": select_ms / args.steps,
+            "e2e": {"value": e2e_u / e2e_s, "unit": "RR-sets/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3))},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": "sample_ic_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg_bytes / max(tk["kernel_launches"], 1),
+                         "avg_launch_ms": tk["kernel_ms"] / max(tk["kernel_launches"], 1),
+                         "large_pass_launches": tk["large_launches"]},
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g, budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps; the timing rules want at least 3", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -155,11 +155,18 @@ gim_status gim_coverage_export(gim_ctx *ctx, uint32_t *cnt_out);
 
 /*
  * Per-phase device times of the last gim_imm / gim_sample_rr /
- * gim_select_seeds call, in milliseconds, from CUDA events:
- * out[0] sampling, out[1] selection (index build + greedy rounds),
- * out[2] wall time of the call, out[3] lower-bound rounds run by gim_imm.
+ * gim_select_seeds call, in milliseconds, from CUDA events on the
+ * context's stream: out[0] sampling, out[1] selection (index build +
+ * greedy rounds), out[2] host wall time of the call, out[3] lower-bound
+ * rounds run by gim_imm. Accumulated since gim_reset_timings (or context
+ * creation): out[4] time inside the common-case sampling kernel and out[5]
+ * its launches; out[6], out[7] the same for the large-set pass.
+ * out must hold 8 doubles.
  */
-gim_status gim_last_timings(gim_ctx *ctx, double out[4]);
+gim_status gim_last_timings(gim_ctx *ctx, double out[8]);
+
+/* Zeroes the accumulated kernel counters of gim_last_timings (out[4..7]). */
+gim_status gim_reset_timings(gim_ctx *ctx);
 
 /* Number of kernels this context has launched since it was created. */
 gim_status gim_launch_count(gim_ctx *ctx, uint64_t *out);

@@ -1,0 +1,189 @@
+"""Thin ctypes binding of libgim's C ABI (include/gim.h).
+
+Argument marshalling only: every step of sampling, selection and IMM runs in
+libgim's CUDA kernels. There is no fallback: if libgim.so has not been built
+(``__graft_entry__.build()`` or ``python -m paper_2009_07325_gb300.build``)
+or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgim.so")
+
+GIM_IC, GIM_LT = 0, 1
+STATUS = {0: "GIM_OK", 1: "GIM_ERR_ARG", 2: "GIM_ERR_OOM", 3: "GIM_ERR_CUDA", 4: "GIM_ERR_TIMEOUT",
+          5: "GIM_ERR_STATE"}
+
+_lock = threading.Lock()
+_lib = None
+
+_c_u32p = ctypes.POINTER(ctypes.c_uint32)
+_c_u64p = ctypes.POINTER(ctypes.c_uint64)
+_c_f32p = ctypes.POINTER(ctypes.c_float)
+_c_f64p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes), mirroring include/gim.h
+SIGNATURES = {
+    "gim_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "gim_destroy": (None, [_vp]),
+    "gim_graph_load": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint64, _c_u64p, _c_u32p, _c_f32p]),
+    "gim_graph_lt_valid": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "gim_sample_rr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]),
+    "gim_reset_rr": (ctypes.c_int, [_vp]),
+    "gim_select_seeds": (ctypes.c_int, [_vp, ctypes.c_uint32, _c_u32p, _c_u64p, _c_u32p]),
+    "gim_imm": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_uint64, _c_u32p, _c_u64p, _c_f64p]),
+    "gim_rr_count": (ctypes.c_int, [_vp, _c_u64p, _c_u64p]),
+    "gim_rr_export": (ctypes.c_int, [_vp, _c_u64p, _c_u32p]),
+    "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
+    "gim_last_timings": (ctypes.c_int, [_vp, _c_f64p]),
+    "gim_reset_timings": (ctypes.c_int, [_vp]),
+    "gim_launch_count": (ctypes.c_int, [_vp, _c_u64p]),
+    "gim_last_error_string": (ctypes.c_char_p, [_vp]),
+}
+
+
+class GimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libgim.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgim.so not found at {path}: build it first "
+                                   "(python -m paper_2009_07325_gb300.build)")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ct)
+
+
+class Context:
+    """One libgim context: a graph, an RR collection and device scratch on one GPU."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.L = load_library()
+        h = _vp()
+        st = self.L.gim_create(ctypes.byref(h), device, _vp(stream) if stream else None)
+        if st != 0:
+            raise GimError(st, f"gim_create(device={device}) failed")
+        self.h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gim_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            msg = self.L.gim_last_error_string(self.h)
+            raise GimError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    # --- API ---------------------------------------------------------------
+    def graph_load(self, n: int, offsets, sources, weights):
+        off = np.ascontiguousarray(offsets, np.uint64)
+        src = np.ascontiguousarray(sources, np.uint32)
+        w = np.ascontiguousarray(weights, np.float32)
+        m = int(off[-1]) if off.size else 0
+        if off.size != n + 1:
+            raise ValueError("offsets must have n+1 entries")
+        if src.size < m or w.size < m:
+            raise ValueError("sources/weights shorter than m")
+        self._check(self.L.gim_graph_load(self.h, n, m, _p(off, _c_u64p), _p(src, _c_u32p), _p(w, _c_f32p)),
+                    "gim_graph_load")
+        self.n = n
+
+    def load(self, graph):
+        self.graph_load(graph.n, graph.offsets, graph.sources, graph.weights)
+
+    @property
+    def lt_valid(self) -> bool:
+        v = ctypes.c_int(0)
+        self._check(self.L.gim_graph_lt_valid(self.h, ctypes.byref(v)), "gim_graph_lt_valid")
+        return bool(v.value)
+
+    def sample_rr(self, model: int, count: int, seed: int):
+        self._check(self.L.gim_sample_rr(self.h, model, count, seed), "gim_sample_rr")
+
+    def reset_rr(self):
+        self._check(self.L.gim_reset_rr(self.h), "gim_reset_rr")
+
+    def select_seeds(self, k: int):
+        seeds = np.zeros(k, np.uint32)
+        gains = np.zeros(k, np.uint32)
+        cov = ctypes.c_uint64(0)
+        self._check(self.L.gim_select_seeds(self.h, k, _p(seeds, _c_u32p), ctypes.byref(cov), _p(gains, _c_u32p)),
+                    "gim_select_seeds")
+        return seeds, gains, int(cov.value)
+
+    def imm(self, model: int, k: int, eps: float, ell: float, seed: int):
+        seeds = np.zeros(k, np.uint32)
+        theta = ctypes.c_uint64(0)
+        lb = ctypes.c_double(0)
+        self._check(self.L.gim_imm(self.h, model, k, eps, ell, seed, _p(seeds, _c_u32p), ctypes.byref(theta),
+                                   ctypes.byref(lb)), "gim_imm")
+        return dict(seeds=seeds, theta=int(theta.value), lb=float(lb.value), rr_count=self.rr_count()[0])
+
+    def rr_count(self):
+        c = ctypes.c_uint64(0)
+        z = ctypes.c_uint64(0)
+        self._check(self.L.gim_rr_count(self.h, ctypes.byref(c), ctypes.byref(z)), "gim_rr_count")
+        return int(c.value), int(z.value)
+
+    def rr_export(self):
+        R, Z = self.rr_count()
+        off = np.zeros(R + 1, np.uint64)
+        mem = np.zeros(max(Z, 1), np.uint32)
+        self._check(self.L.gim_rr_export(self.h, _p(off, _c_u64p), _p(mem, _c_u32p)), "gim_rr_export")
+        return off, mem[:Z]
+
+    def coverage(self) -> np.ndarray:
+        out = np.zeros(max(self.n, 1), np.uint32)
+        self._check(self.L.gim_coverage_export(self.h, _p(out, _c_u32p)), "gim_coverage_export")
+        return out[: self.n]
+
+    def timings(self) -> dict:
+        out = np.zeros(8, np.float64)
+        self._check(self.L.gim_last_timings(self.h, _p(out, _c_f64p)), "gim_last_timings")
+        return dict(sample_ms=out[0], select_ms=out[1], wall_ms=out[2], lb_rounds=int(out[3]),
+                    kernel_ms=out[4], kernel_launches=int(out[5]), large_ms=out[6], large_launches=int(out[7]))
+
+    def reset_timings(self):
+        self._check(self.L.gim_reset_timings(self.h), "gim_reset_timings")
+
+    def launch_count(self) -> int:
+        c = ctypes.c_uint64(0)
+        self._check(self.L.gim_launch_count(self.h, ctypes.byref(c)), "gim_launch_count")
+        return int(c.value)

@@ -1,0 +1,200 @@
+"""GPU parity: libgim (through the C ABI) against the CPU oracle, bit-exact.
+
+RR sets (as sorted vertex lists per rr_id), occurrence counts, seed lists,
+marginal gains, covered counts, theta and LB must be identical. Inputs are
+seeded synthetic graphs of the paper's kind (Sec. IV-B weighting): a directed
+Erdos-Renyi graph (n = 2000, m = 20000), R-MAT scale 20 and 22 with
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), weighted-cascade probabilities and
+uniform p = 0.01. Edge cases: p = 0 and p = 1, n = 2, k = n, empty
+collection, RR sets larger than a worker's queue (the large-set pass) and a
+store that must grow mid-call.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context, GimError
+from paper_2009_07325_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, O.max_threads())
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2009_07325_gb300 import build
+    build.build()
+    O.build()
+    I.build()
+
+
+@pytest.fixture(scope="module")
+def er_wc():
+    return I.wc_weights(I.er(2000, 20000, 1))
+
+
+@pytest.fixture(scope="module")
+def rmat20_wc():
+    return I.wc_weights(I.rmat(20, 2))
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    return I.rmat(22, 3)
+
+
+def _ctx(g):
+    c = Context(0)
+    c.load(g)
+    return c
+
+
+def _same_collection(ctx, orc):
+    off_g, mem_g = ctx.rr_export()
+    off_o, mem_o = orc.export()
+    assert off_g.shape == off_o.shape
+    if not np.array_equal(off_g, off_o):
+        bad = int(np.nonzero(off_g != off_o)[0][0])
+        raise AssertionError(f"first differing RR set near rr_id {bad - 1}")
+    assert np.array_equal(mem_g, mem_o)
+    assert np.array_equal(ctx.coverage(), orc.counts())
+
+
+@pytest.mark.parametrize("model", [GIM_IC, GIM_LT])
+def test_er_sample_select_bit_exact(er_wc, model):
+    ctx = _ctx(er_wc)
+    orc = O.Oracle(er_wc)
+    for count in (1, 999, 4000):       # several appends: ids continue across calls
+        ctx.sample_rr(model, count, 7)
+        orc.sample(model, 7, count, THREADS)
+    _same_collection(ctx, orc)
+    for k in (1, 10, 64):
+        assert [a.tolist() if hasattr(a, "tolist") else a for a in ctx.select_seeds(k)] == \
+               [a.tolist() if hasattr(a, "tolist") else a for a in orc.greedy(k)]
+
+
+@pytest.mark.parametrize("model,k,eps", [(GIM_IC, 10, 0.5), (GIM_LT, 10, 0.5), (GIM_IC, 25, 0.3)])
+def test_er_imm_bit_exact(er_wc, model, k, eps):
+    ctx = _ctx(er_wc)
+    orc = O.Oracle(er_wc)
+    g = ctx.imm(model, k, eps, 1.0, 7)
+    o = orc.imm(model, k, eps, 1.0, 7, THREADS)
+    assert g["seeds"].tolist() == o["seeds"].tolist()
+    assert g["theta"] == o["theta"] and g["lb"] == o["lb"] and g["rr_count"] == o["rr_count"]
+    _same_collection(ctx, orc)
+
+
+def test_rmat20_ic_wc_bit_exact(rmat20_wc):
+    ctx = _ctx(rmat20_wc)
+    orc = O.Oracle(rmat20_wc)
+    ctx.sample_rr(GIM_IC, 30000, 7)
+    orc.sample(GIM_IC, 7, 30000, THREADS)
+    _same_collection(ctx, orc)
+    gs, gg, gc = ctx.select_seeds(50)
+    os_, og, oc = orc.greedy(50)
+    assert gs.tolist() == os_.tolist() and gg.tolist() == og.tolist() and gc == oc
+
+
+def test_rmat22_lt_bit_exact(rmat22):
+    g = I.wc_weights(rmat22)
+    ctx = _ctx(g)
+    assert ctx.lt_valid
+    orc = O.Oracle(g)
+    ctx.sample_rr(GIM_LT, 50000, 7)
+    orc.sample(GIM_LT, 7, 50000, THREADS)
+    _same_collection(ctx, orc)
+    gs, gg, gc = ctx.select_seeds(100)
+    os_, og, oc = orc.greedy(100)
+    assert gs.tolist() == os_.tolist() and gg.tolist() == og.tolist() and gc == oc
+
+
+def test_rmat22_ic_p001_giant_sets_bit_exact(rmat22):
+    """Uniform p = 0.01: ~5% of RR sets reach a giant component (> queue capacity)."""
+    g = I.uniform_weights(rmat22, 0.01)
+    ctx = _ctx(g)
+    assert not ctx.lt_valid
+    orc = O.Oracle(g)
+    ctx.sample_rr(GIM_IC, 1500, 7)
+    orc.sample(GIM_IC, 7, 1500, THREADS)
+    _same_collection(ctx, orc)
+    gs, gg, gc = ctx.select_seeds(20)
+    os_, og, oc = orc.greedy(20)
+    assert gs.tolist() == os_.tolist() and gg.tolist() == og.tolist() and gc == oc
+
+
+def test_store_growth_and_large_sets():
+    """p = 1 on a strongly connected ER graph: every RR set is ~n vertices, so each
+    set overflows the worker queue and the store (64M entries) must grow."""
+    g = I.uniform_weights(I.er(20000, 200000, 5), 1.0)
+    ctx = _ctx(g)
+    orc = O.Oracle(g)
+    ctx.sample_rr(GIM_IC, 4000, 3)
+    orc.sample(GIM_IC, 3, 4000, THREADS)
+    _same_collection(ctx, orc)
+    assert ctx.rr_count()[1] > (1 << 26)
+
+
+def test_degenerate_weights_and_sizes():
+    base = I.er(300, 1500, 2)
+    for p in (0.0, 1.0):
+        g = I.uniform_weights(base, p)
+        ctx = _ctx(g)
+        orc = O.Oracle(g)
+        for model in ((GIM_IC, GIM_LT) if p == 0.0 else (GIM_IC,)):
+            ctx.reset_rr()
+            orc.reset()
+            ctx.sample_rr(model, 2000, 11)
+            orc.sample(model, 11, 2000, THREADS)
+            _same_collection(ctx, orc)
+            assert ctx.select_seeds(300)[0].tolist() == orc.greedy(300)[0].tolist()   # k = n
+    # n = 2, a single edge
+    two = I.from_edges(2, [0], [1]).with_weights(np.array([0.5], np.float32), "two")
+    ctx = _ctx(two)
+    orc = O.Oracle(two)
+    ctx.sample_rr(GIM_IC, 100, 1)
+    orc.sample(GIM_IC, 1, 100)
+    _same_collection(ctx, orc)
+    r = ctx.imm(GIM_IC, 1, 0.5, 1.0, 1)
+    o = O.Oracle(two).imm(GIM_IC, 1, 0.5, 1.0, 1)
+    assert r["seeds"].tolist() == o["seeds"].tolist() and r["theta"] == o["theta"] and r["lb"] == o["lb"]
+
+
+def test_empty_collection_selection(er_wc):
+    ctx = _ctx(er_wc)
+    s, gains, cov = ctx.select_seeds(5)
+    assert s.tolist() == [0, 1, 2, 3, 4] and gains.tolist() == [0] * 5 and cov == 0
+
+
+def test_state_and_argument_errors(er_wc):
+    ctx = Context(0)
+    with pytest.raises(GimError):
+        ctx.sample_rr(GIM_IC, 10, 1)            # no graph
+    ctx.load(er_wc)
+    ctx.sample_rr(GIM_IC, 10, 1)
+    with pytest.raises(GimError):
+        ctx.sample_rr(GIM_LT, 10, 1)            # model change needs reset
+    with pytest.raises(GimError):
+        ctx.sample_rr(GIM_IC, 10, 2)            # seed change needs reset
+    assert ctx.rr_count()[0] == 10
+    with pytest.raises(GimError):
+        ctx.select_seeds(2001)
+    with pytest.raises(GimError):
+        ctx.imm(GIM_IC, 5, 1.5, 1.0, 1)
+    bad = I.er(50, 100, 1)
+    with pytest.raises(GimError):            # weight outside [0, 1]
+        ctx.graph_load(50, bad.offsets, bad.sources, np.full(bad.m, 1.5, np.float32))
+    with pytest.raises(GimError):            # source out of range
+        src = bad.sources.copy()
+        src[0] = 50
+        ctx.graph_load(50, bad.offsets, src, np.full(bad.m, 0.5, np.float32))
+    # the failed loads left the previous graph and collection in place
+    assert ctx.rr_count()[0] == 10
+    ctx.reset_rr()
+    assert ctx.rr_count() == (0, 0)
+    ic = I.uniform_weights(I.er(50, 400, 1), 0.9)   # rows sum above 1: not LT-valid
+    ctx.load(ic)
+    assert not ctx.lt_valid
+    with pytest.raises(GimError):
+        ctx.sample_rr(GIM_LT, 10, 1)
+    assert ctx.launch_count() > 0
