@@ -295,6 +295,33 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """Small single-call cases for profiling: one gim_sample_rr / gim_select_seeds on the workload graph."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context
+    from paper_2009_07325_gb300 import inputs as I
+    base = I.rmat(22, 3)
+    g = I.uniform_weights(base, 0.01) if args.case == "sample-ic-p001" else I.wc_weights(base)
+    model = GIM_LT if args.case == "sample-lt" else GIM_IC
+    ctx = Context(0)
+    ctx.load(g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.sample_rr(model, args.count, WORKLOAD["philox_seed"])
+    t_s = time.perf_counter() - t0
+    out = {"case": args.case, "count": args.count, "sample_s": t_s, "timings": ctx.timings(),
+           "members": ctx.rr_count()[1]}
+    if args.case == "select":
+        t0 = time.perf_counter()
+        s, gains, cov = ctx.select_seeds(WORKLOAD["k"])
+        out.update(select_s=time.perf_counter() - t0, covered=cov, timings_select=ctx.timings())
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,9 +331,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, choices=["sample-ic", "sample-lt", "sample-ic-p001", "select"],
+                    help="run one small profiling case instead of the benchmark")
+    ap.add_argument("--count", type=int, default=20000, help="RR sets for --case")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps; the timing rules want at least 3", file=sys.stderr)
+    if args.case:
+        return run_case(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

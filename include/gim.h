@@ -5,9 +5,9 @@
  * Salehkaleybar, Hashemi, "gIM: GPU Accelerated RIS-based Influence
  * Maximization Algorithm", IEEE TPDS; arXiv 2009.07325):
  *   - RR-set sampling under the IC and LT diffusion models (Sec. III-B,
- *     Alg. 3 and 6; Sec. III-F),
- *   - greedy maximum coverage over the RR sets (Alg. 1 lines 6-10,
- *     Sec. III-G, Alg. 7),
+ *     Alg. 3 and 6; Sec. III-G),
+ *   - greedy maximum coverage over the RR sets (the maximum-coverage step of Alg. 1,
+ *     Sec. III-H, Alg. 7),
  *   - IMM's lower-bound search and theta in FP64 on the host (Alg. 2).
  *
  * Conventions shared by every entry point:
@@ -75,7 +75,7 @@ void gim_destroy(gim_ctx *ctx);
  *   in_sources: m entries, each < n, strictly ascending within a row.
  *   in_weights: m entries.
  * Precomputes the IC coin thresholds and the LT cumulative thresholds
- * (Sec. III-F). The graph is usable under LT only if every row's weights
+ * (Sec. III-G). The graph is usable under LT only if every row's weights
  * sum to at most 1 + 1e-6 (Sec. II-B); gim_graph_lt_valid reports it.
  * Replaces any previous graph and empties the RR collection.
  * Limits: 2 <= n < 2^32 - 1, m < 2^32 - 4.
@@ -90,11 +90,11 @@ gim_status gim_graph_lt_valid(gim_ctx *ctx, int *out);
 
 /*
  * Appends `count` random RR sets with ids |R| .. |R|+count-1 to the
- * context's collection R (Alg. 1 line 4; Alg. 6), drawn under `model` with
+ * context's collection R (the sampling step of Alg. 1; Alg. 6), drawn under `model` with
  * the 64-bit `seed`. IC: the vertices from which the root reaches along
  * live edges, each in-edge live with its probability (Sec. II-E, Alg. 3).
  * LT: the walk that, at each vertex, picks at most one in-edge with
- * probability equal to its weight (Sec. III-F). The occurrence counts
+ * probability equal to its weight (Sec. III-G). The occurrence counts
  * (Occur of Sec. III-B) are updated.
  * Errors: GIM_ERR_STATE (no graph; or model/seed differ from those of a
  * non-empty collection: call gim_reset_rr first), GIM_ERR_ARG (LT on a
@@ -107,8 +107,8 @@ gim_status gim_sample_rr(gim_ctx *ctx, gim_model model, uint64_t count, uint64_t
 gim_status gim_reset_rr(gim_ctx *ctx);
 
 /*
- * Greedy maximum coverage over the collection (Alg. 1 lines 6-10;
- * Sec. III-G): k rounds, each taking the vertex outside the seed set that
+ * Greedy maximum coverage over the collection (the maximum-coverage step of Alg. 1;
+ * Sec. III-H): k rounds, each taking the vertex outside the seed set that
  * lies in the most RR sets not yet covered (lowest id on ties), then
  * removing the RR sets it covers. Once all sets are covered, the remaining
  * rounds take the lowest unselected ids with gain 0.

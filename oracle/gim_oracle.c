@@ -85,7 +85,7 @@ int orc_ic_live(uint64_t seed, uint64_t j, uint64_t e, float p) {
   return u < p;
 }
 
-/* The single uniform drawn at vertex x of an LT walk (Sec. III-F). */
+/* The single uniform drawn at vertex x of an LT walk (Sec. III-G). */
 uint32_t orc_lt_draw(uint64_t seed, uint64_t j, uint32_t x) {
   uint32_t w[4];
   draw4(seed, j, 2, x, w);
@@ -114,7 +114,7 @@ typedef struct orc {
 } orc;
 
 /*
- * LT cumulative thresholds for every row (Sec. III-F: the scan over in-edge
+ * LT cumulative thresholds for every row (Sec. III-G: the scan over in-edge
  * weights whose consecutive outputs bracket the uniform draw), in 2^-32
  * units so that the bracket test is an exact integer compare.
  */
@@ -201,7 +201,7 @@ static uint32_t rr_ic(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited,
 }
 
 /*
- * LT RR set j (Sec. III-F): at each vertex one uniform draw selects at most
+ * LT RR set j (Sec. III-G): at each vertex one uniform draw selects at most
  * one live in-edge (the edge whose threshold interval contains the draw);
  * the walk moves to its source and stops when no edge is selected or the
  * source was already visited. Same scratch contract as rr_ic.
@@ -263,7 +263,7 @@ static int grow_members(orc *g, uint64_t need) {
 typedef struct { uint64_t n_sets, n_members, cap; uint32_t *mem; uint32_t *sizes; } chunk_buf;
 
 /*
- * Appends RR sets |R| .. |R|+count-1 to R (Alg. 1 line 4; Alg. 2 line 5).
+ * Appends RR sets |R| .. |R|+count-1 to R (the sampling steps of Alg. 1 and Alg. 2).
  * With threads > 1 the rr_id range is split into contiguous chunks, one per
  * thread, and the chunks are concatenated in order, so R is the same as with
  * one thread. Returns 0, -1 (model/seed differ from the stored collection,
@@ -360,7 +360,7 @@ void orc_counts(const orc *g, uint32_t *cnt) {
 }
 
 /*
- * Greedy maximum coverage over R (Alg. 1 lines 6-10; Sec. III-G): k times,
+ * Greedy maximum coverage over R (the maximum-coverage step of Alg. 1; Sec. III-H): k times,
  * take the unselected vertex that lies in the most uncovered RR sets (lowest
  * id on ties), record that number as its marginal gain, and remove every RR
  * set containing it, lowering the counts of all their members. The sets that

@@ -1,6 +1,6 @@
 // Graph preprocessing on the device: validation of the in-edge CSR, the IC
 // coin thresholds and the LT cumulative thresholds (Sec. III-B CSR layout;
-// Sec. III-F LT edge choice).
+// Sec. III-G LT edge choice).
 #include <algorithm>
 
 #include "gim_internal.cuh"

@@ -1,4 +1,4 @@
-// RR-set sampling kernels (Sec. III-B to III-F; Alg. 3 and Alg. 6).
+// RR-set sampling kernels (Sec. III-B to III-G; Alg. 3 and Alg. 6).
 //
 // A persistent grid of warps; each warp is one worker that takes RR-set ids
 // from a device work counter (the role of Alg. 6's N_RR) and builds one RR
@@ -10,7 +10,7 @@
 //       A live edge whose source is not yet visited marks it in the worker's
 //       visited bitmap and appends it to the worker's queue, which doubles as
 //       the member list (Sec. III-A: each vertex is expanded once).
-//   LT: the reverse walk of Sec. III-F: one draw per step, the chosen in-edge
+//   LT: the reverse walk of Sec. III-G: one draw per step, the chosen in-edge
 //       found by a 33-way warp search over the row's sorted cumulative
 //       thresholds, stop at no edge or at a vertex already on the path.
 // A finished set reserves its place in the store with one atomic (Alg. 6's

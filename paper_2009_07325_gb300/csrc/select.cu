@@ -1,12 +1,12 @@
-// Greedy maximum coverage over the RR collection (Alg. 1 lines 6-10;
-// Sec. III-G, Alg. 7), on the device.
+// Greedy maximum coverage over the RR collection (the maximum-coverage step of Alg. 1;
+// Sec. III-H, Alg. 7), on the device.
 //
 // Instead of Alg. 7's scan of the whole RR store for every seed, a
 // vertex -> RR-set inverted index is built once per call (exclusive scan of
 // the occurrence counts, then a fill), so a round only touches the RR sets
 // that contain the new seed. Each round is two kernels:
 //   argmax: the unselected vertex with the largest count, lowest id on ties
-//           (the max-reduction of Sec. III-G), as a max over 64-bit keys
+//           (the max-reduction of Sec. III-H), as a max over 64-bit keys
 //           (count+1) << 32 | ~id; a selected vertex has key ~id < 2^32;
 //   cover:  every RR set containing the seed that is not yet covered is
 //           flagged covered and the counts of its members are lowered.

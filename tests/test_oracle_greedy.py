@@ -1,4 +1,4 @@
-"""Pins of the oracle's greedy maximum coverage (Alg. 1 lines 6-10).
+"""Pins of the oracle's greedy maximum coverage (the maximum-coverage step of Alg. 1).
 
 Checked against brute force on small hand-made and random set systems: each
 round's pick maximises the marginal coverage (lowest id on ties), coverage
