@@ -34,9 +34,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IMM end-to-end s & RR-sets/s (IC, R-MAT-22, k=50, ε=0.1); % HBM peak"
-WORKLOAD = dict(workload="imm-ic-wc-rmat22", graph="R-MAT scale 22 (16*2^22 draws, a,b,c,d=.57/.19/.19/.05, "
-                "dedup, seed 3)", weights="weighted cascade 1/indeg(v) fp32", model="IC", k=50, eps=0.1, ell=1.0,
-                philox_seed=7)
+_RMAT = "R-MAT scale {s} (16*2^{s} draws, a,b,c,d=.57/.19/.19/.05, dedup, seed {seed})"
+WORKLOADS = {
+    # the headline: IC weighted cascade on the R-MAT scale-22 graph
+    "imm-ic-wc-rmat22": dict(graph=_RMAT.format(s=22, seed=3), weights="weighted cascade 1/indeg(v) fp32",
+                             model="IC", k=50, eps=0.1, ell=1.0, philox_seed=7),
+    # the same graph under LT (in-weights 1/indeg(v)), k=100, eps=0.05
+    "imm-lt-wc-rmat22": dict(graph=_RMAT.format(s=22, seed=3), weights="LT 1/indeg(v) fp32",
+                             model="LT", k=100, eps=0.05, ell=1.0, philox_seed=7),
+    # R-MAT scale 20, IC weighted cascade, k=50, eps=0.1
+    "imm-ic-wc-rmat20": dict(graph=_RMAT.format(s=20, seed=2), weights="weighted cascade 1/indeg(v) fp32",
+                             model="IC", k=50, eps=0.1, ell=1.0, philox_seed=7),
+    # directed Erdos-Renyi n=2000, m=20000, IC weighted cascade, k=10, eps=0.5
+    "imm-ic-wc-er2000": dict(graph="directed Erdos-Renyi n=2000 m=20000 seed 1",
+                             weights="weighted cascade 1/indeg(v) fp32", model="IC", k=10, eps=0.5, ell=1.0,
+                             philox_seed=7),
+}
+WORKLOAD = dict(workload="imm-ic-wc-rmat22", **WORKLOADS["imm-ic-wc-rmat22"])
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -143,13 +157,30 @@ class ClockSampler:
 
 def load_workload():
     from paper_2009_07325_gb300 import inputs as I
-    return I.wc_weights(I.rmat(22, 3))
+    name = WORKLOAD["workload"]
+    if name.endswith("rmat22"):
+        return I.wc_weights(I.rmat(22, 3))
+    if name.endswith("rmat20"):
+        return I.wc_weights(I.rmat(20, 2))
+    return I.wc_weights(I.er(2000, 20000, 1))
+
+
+def model_id():
+    from paper_2009_07325_gb300 import GIM_IC, GIM_LT
+    return GIM_LT if WORKLOAD["model"] == "LT" else GIM_IC
+
+
+def coin_count(cnt: np.ndarray, indeg: np.ndarray) -> float:
+    """IC sampling work: one coin per in-edge of every expanded vertex, i.e.
+    sum over RR-set members v of indeg(v) (four coins per Philox call)."""
+    return float(np.dot(cnt.astype(np.float64), indeg.astype(np.float64)))
 
 
 def algorithmic_bytes(cnt: np.ndarray, indeg: np.ndarray) -> float:
-    """IC sampling: per member v of an RR set, 8 B of offsets, 8 B per in-edge
-    (source + coin threshold), 4 B store write, 4 B count update."""
-    return float(np.dot(cnt.astype(np.float64), 16.0 + 8.0 * indeg.astype(np.float64)))
+    """IC sampling memory per member v on a row with a common threshold:
+    8 B offsets + 4 B row threshold + 4 B store write + 4 B count update
+    (sources of live edges, about one per row under weighted cascade, add 4 B)."""
+    return float(cnt.astype(np.float64).sum() * 24.0)
 
 
 def cpu_baseline(graph, budget_s: float = 12.0):
@@ -161,12 +192,12 @@ def cpu_baseline(graph, budget_s: float = 12.0):
     t0 = time.perf_counter()
     chunk = 4000
     while time.perf_counter() - t0 < budget_s:
-        o.sample(O.IC, WORKLOAD["philox_seed"], chunk, th)
+        o.sample(O.LT if WORKLOAD["model"] == "LT" else O.IC, WORKLOAD["philox_seed"], chunk, th)
     o.greedy(WORKLOAD["k"])
     dt = time.perf_counter() - t0
     n = o.rr_count
     return {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle",
-            "sample": f"{n} IC RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
+            "sample": f"{n} {WORKLOAD['model']} RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
                       f"{dt:.1f} s"}
 
 
@@ -213,12 +244,13 @@ def run_ours(args):
     k, eps, ell, seed = WORKLOAD["k"], WORKLOAD["eps"], WORKLOAD["ell"], WORKLOAD["philox_seed"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=f"cuda:{local}")
 
+    mdl = model_id()
     for _ in range(args.warmup):
-        ctx.imm(GIM_IC, k, eps, ell, seed)
+        ctx.imm(mdl, k, eps, ell, seed)
 
     ctx.reset_timings()
     launches0 = ctx.launch_count()
-    step_ms, rr_sets, alg_bytes, sample_ms, select_ms, thetas = [], 0, 0.0, 0.0, 0.0, []
+    step_ms, rr_sets, alg_bytes, coins, sample_ms, select_ms, thetas = [], 0, 0.0, 0.0, 0.0, 0.0, []
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -228,7 +260,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = ctx.imm(GIM_IC, k, eps, ell, seed)
+            r = ctx.imm(mdl, k, eps, ell, seed)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -237,11 +269,14 @@ def run_ours(args):
             select_ms += t["select_ms"]
             rr_sets += r["rr_count"]
             thetas.append(r["theta"])
-            alg_bytes += algorithmic_bytes(ctx.coverage(), indeg)
+            cov = ctx.coverage()
+            alg_bytes += algorithmic_bytes(cov, indeg)
+            coins += coin_count(cov, indeg)
     torch.cuda.synchronize()
     barrier()
     tk = ctx.timings()
     launches = ctx.launch_count() - launches0
+    philox_calls_per_s = ctx.philox_rate()       # measured ALU ceiling (after the timed region)
     local_s = sum(step_ms) / 1e3
     units, secs = aggregate(float(rr_sets), local_s)
 
@@ -254,20 +289,23 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.graph_load(g.n, off_p, src_p, w_p)
-        r = ctx.imm(GIM_IC, k, eps, ell, seed)
+        r = ctx.imm(mdl, k, eps, ell, seed)
         e2e_t += time.perf_counter() - t0
         e2e_units += r["rr_count"]
     e2e_u, e2e_s = aggregate(float(e2e_units), e2e_t)
     d2h = 4 * k + 8 + 8
 
     if rank == 0:
-        peak, peak_kind = measured_peaks()
-        achieved = alg_bytes / (tk["kernel_ms"] / 1e3) / 1e9 if tk["kernel_ms"] > 0 else 0.0
+        hbm_peak, peak_kind = measured_peaks()
+        kern_s = (tk["kernel_ms"] + tk["large_ms"]) / 1e3
+        n_launch = max(tk["kernel_launches"] + tk["large_launches"], 1)
+        achieved = coins / kern_s / 1e9 if kern_s > 0 else 0.0          # G coins / s
+        peak = 4.0 * philox_calls_per_s / 1e9                            # G coins / s, measured
         tr = traffic_record("sample_ic_kernel")
         traffic = None
         if tr is not None:
             per_unit, unit = tr
-            traffic = per_unit * (rr_sets / max(tk["kernel_launches"], 1)) if unit == "rr_set" else None
+            traffic = per_unit * (rr_sets / n_launch) if unit == "rr_set" else None
         line = {
             "metric": METRIC, "value": units / secs, "unit": "RR-sets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -278,11 +316,14 @@ def run_ours(args):
             "e2e": {"value": e2e_u / e2e_s, "unit": "RR-sets/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3))},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": "sample_ic_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": alg_bytes / max(tk["kernel_launches"], 1),
-                         "avg_launch_ms": tk["kernel_ms"] / max(tk["kernel_launches"], 1),
-                         "large_pass_launches": tk["large_launches"]},
+            "roofline": {"bound": "alu", "kernel": "sample_ic_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "Gcoins/s", "frac": achieved / peak,
+                         "peak_kind": "measured: pure Philox4x32-10 kernel on this GPU, 4 coins per call",
+                         "traffic": traffic, "coins_per_launch": coins / n_launch,
+                         "avg_launch_ms": 1e3 * kern_s / n_launch, "launches": n_launch,
+                         "large_pass_launches": tk["large_launches"],
+                         "hbm_view": {"algorithmic_gbs": alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0,
+                                      "peak_gbs": hbm_peak, "peak_kind": peak_kind}},
             "clocks": clk.summary(),
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -334,9 +375,13 @@ def main():
     ap.add_argument("--case", default=None, choices=["sample-ic", "sample-lt", "sample-ic-p001", "select"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--count", type=int, default=20000, help="RR sets for --case")
+    ap.add_argument("--workload", default="imm-ic-wc-rmat22", choices=sorted(WORKLOADS),
+                    help="IMM workload (default: the headline)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps; the timing rules want at least 3", file=sys.stderr)
+    WORKLOAD.clear()
+    WORKLOAD.update(workload=args.workload, **WORKLOADS[args.workload])
     if args.case:
         return run_case(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -168,6 +168,14 @@ gim_status gim_last_timings(gim_ctx *ctx, double out[8]);
 /* Zeroes the accumulated kernel counters of gim_last_timings (out[4..7]). */
 gim_status gim_reset_timings(gim_ctx *ctx);
 
+/*
+ * Diagnostic: the device's throughput of Philox4x32-10 blocks (the coin
+ * generator of Alg. 3's "p = U(0,1)") measured by a kernel that does nothing
+ * else, in calls per second (best of three timed launches after a warm-up).
+ * This is the integer-ALU ceiling of the IC sampler's coin work.
+ */
+gim_status gim_diag_philox_rate(gim_ctx *ctx, double *calls_per_s);
+
 /* Number of kernels this context has launched since it was created. */
 gim_status gim_launch_count(gim_ctx *ctx, uint64_t *out);
 

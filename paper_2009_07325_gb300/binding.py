@@ -45,6 +45,7 @@ SIGNATURES = {
     "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
     "gim_last_timings": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_reset_timings": (ctypes.c_int, [_vp]),
+    "gim_diag_philox_rate": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_launch_count": (ctypes.c_int, [_vp, _c_u64p]),
     "gim_last_error_string": (ctypes.c_char_p, [_vp]),
 }
@@ -182,6 +183,12 @@ class Context:
 
     def reset_timings(self):
         self._check(self.L.gim_reset_timings(self.h), "gim_reset_timings")
+
+    def philox_rate(self) -> float:
+        """Measured Philox4x32-10 calls per second of this device (ALU ceiling of the coins)."""
+        out = ctypes.c_double(0)
+        self._check(self.L.gim_diag_philox_rate(self.h, ctypes.byref(out)), "gim_diag_philox_rate")
+        return float(out.value)
 
     def launch_count(self) -> int:
         c = ctypes.c_uint64(0)

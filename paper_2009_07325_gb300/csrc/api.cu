@@ -53,6 +53,7 @@ void free_graph(DevGraph &g) {
   dfree(g.off);
   dfree(g.src);
   dfree(g.thr);
+  dfree(g.rthr);
   dfree(g.cum);
   g = DevGraph{};
 }
@@ -384,6 +385,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   if ((e = cudaMalloc(&g.off, ((uint64_t)n + 1) * 4)) != cudaSuccess) return bail(e, "alloc offsets");
   if ((e = cudaMalloc(&g.src, m_pad * 4)) != cudaSuccess) return bail(e, "alloc sources");
   if ((e = cudaMalloc(&g.thr, m_pad * 4)) != cudaSuccess) return bail(e, "alloc thresholds");
+  if ((e = cudaMalloc(&g.rthr, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row thresholds");
   if ((e = cudaMalloc(&g.cum, std::max<uint64_t>(m, 1) * 8)) != cudaSuccess) return bail(e, "alloc lt thresholds");
   if ((e = cudaMalloc(&d_w, std::max<uint64_t>(m, 1) * 4)) != cudaSuccess) return bail(e, "alloc weights");
   if ((e = cudaMalloc(&d_flags, 4)) != cudaSuccess) return bail(e, "alloc flags");
@@ -635,6 +637,34 @@ gim_status gim_reset_timings(gim_ctx *ctx) {
   if (!ctx) return GIM_ERR_ARG;
   ctx->t_kernel_ms[0] = ctx->t_kernel_ms[1] = 0;
   ctx->n_kernel[0] = ctx->n_kernel[1] = 0;
+  return GIM_OK;
+}
+
+gim_status gim_diag_philox_rate(gim_ctx *ctx, double *calls_per_s) {
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!calls_per_s) return set_err(ctx, GIM_ERR_ARG, "calls_per_s is null");
+  uint32_t *sink = nullptr;
+  CU(cudaMalloc(&sink, 1024 * 4));
+  const int blocks = ctx->sm_count * 8;
+  const uint32_t per_thread = 4096;
+  float best = 0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(ctx->ev[6], ctx->stream);
+    cudaError_t e = launch_philox_rate(blocks, per_thread, sink, ctx->stream);
+    cudaEventRecord(ctx->ev[7], ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev[7]);
+    if (e != cudaSuccess) {
+      cudaFree(sink);
+      return cuda_err(ctx, e, "philox rate kernel");
+    }
+    ctx->launches++;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);
+    if (rep > 0 && (best == 0 || ms < best)) best = ms;
+  }
+  cudaFree(sink);
+  *calls_per_s = (double)blocks * 256.0 * per_thread / (best / 1e3);
   return GIM_OK;
 }
 

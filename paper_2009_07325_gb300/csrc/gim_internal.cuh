@@ -59,8 +59,11 @@ struct DevGraph {
   uint32_t *off = nullptr;   // n+1
   uint32_t *src = nullptr;   // m rounded up to a multiple of 4, zero padded
   uint32_t *thr = nullptr;   // same length: IC coin threshold ceil(w * 2^24)
+  uint32_t *rthr = nullptr;  // n: the row's common threshold when all its in-edges share one, else kPerEdge
   uint64_t *cum = nullptr;   // m: LT cumulative thresholds in 2^-32 units
 };
+
+constexpr uint32_t kPerEdge = 0xFFFFFFFFu;   // rthr value of a row whose thresholds differ
 
 // Output side of a sampling launch.
 struct DevStore {
@@ -105,6 +108,7 @@ struct SampleJob {
 cudaError_t launch_sample(int model, const DevGraph &g, const DevStore &st, const WorkerScratch &ws, const SampleJob &job,
                           SampleCtl *ctl, bool large, int grid, int block, cudaStream_t s);
 cudaError_t launch_uncount(const DevStore &st, uint64_t j_begin, uint64_t count, cudaStream_t s);
+cudaError_t launch_philox_rate(int blocks, uint32_t per_thread, uint32_t *sink, cudaStream_t s);
 
 // Graph preprocessing (graph.cu).
 cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_flags, cudaStream_t s);

@@ -29,30 +29,59 @@ __global__ void prep_edges_kernel(uint32_t n, uint64_t m, uint64_t m_pad, const 
   if (bad) atomicOr(flags, bad);
 }
 
-// Row-parallel: ascending sources within a row, and the LT thresholds.
+// Warp per row: ascending sources within the row, the row's common IC
+// threshold (rthr), and the LT thresholds.
 // cum[e_i] = min(2^32, round_half_up(P_i * 2^32)), P_i the fp64 running sum of
 // the row's weights in CSR order; a row summing to within 1e-6 of 1 gets
 // cum[last] = 2^32 so that it always selects an edge. A row summing above
-// 1 + 1e-6 marks the graph as not valid for LT.
-__global__ void prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off, const uint32_t *__restrict__ src,
-                                 const float *__restrict__ w, uint64_t *__restrict__ cum,
-                                 unsigned int *__restrict__ flags) {
+// 1 + 1e-6 marks the graph as not valid for LT. The loads are coalesced; the
+// running sum stays strictly sequential (every lane adds the 32 broadcast
+// weights of a chunk in order and keeps the prefix that ends at its edge).
+__global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off,
+                                                        const uint32_t *__restrict__ src,
+                                                        const float *__restrict__ w,
+                                                        const uint32_t *__restrict__ thr,
+                                                        uint32_t *__restrict__ rthr, uint64_t *__restrict__ cum,
+                                                        unsigned int *__restrict__ flags) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned int bad = 0;
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+  for (uint32_t v = warp; v < n; v += nwarps) {
     const uint32_t s = off[v], e = off[v + 1];
+    const uint32_t common0 = e > s ? thr[s] : 0u;
+    bool differs = false;
     double P = 0.0;
-    for (uint32_t i = s; i < e; ++i) {
-      if (i > s && !(src[i - 1] < src[i])) bad |= kGraphNotAscending;
-      P = __dadd_rn(P, (double)w[i]);
-      const double x = __dmul_rn(P, 4294967296.0);
-      const double f = floor(x);
-      unsigned long long c = (unsigned long long)f;
-      if (__dsub_rn(x, f) >= 0.5) c += 1ull;
-      if (c > 4294967296ull) c = 4294967296ull;
-      cum[i] = c;
+    for (uint32_t base = s; base < e; base += 32) {
+      const uint32_t i = base + lane;
+      const bool in = i < e;
+      const float wi = in ? w[i] : 0.0f;
+      const uint32_t si = in ? src[i] : 0u;
+      if (in && thr[i] != common0) differs = true;
+      uint32_t prev = __shfl_up_sync(kFullMask, si, 1);
+      if (lane == 0 && base > s) prev = src[base - 1];
+      if (in && i > s && !(prev < si)) bad |= kGraphNotAscending;
+      const uint32_t cnt = e - base < 32u ? e - base : 32u;
+      double mine = 0.0;
+      for (uint32_t t = 0; t < cnt; ++t) {
+        P = __dadd_rn(P, (double)__shfl_sync(kFullMask, wi, t));
+        if (t == lane) mine = P;
+      }
+      if (in) {
+        const double x = __dmul_rn(mine, 4294967296.0);
+        const double f = floor(x);
+        unsigned long long c = (unsigned long long)f;
+        if (__dsub_rn(x, f) >= 0.5) c += 1ull;
+        if (c > 4294967296ull) c = 4294967296ull;
+        cum[i] = c;
+      }
     }
-    if (e > s && fabs(__dsub_rn(P, 1.0)) <= 1e-6) cum[e - 1] = 4294967296ull;
-    if (P > 1.0 + 1e-6) bad |= kGraphNotLT;
+    const bool any_diff = __any_sync(kFullMask, differs);
+    if (lane == 0) {
+      rthr[v] = any_diff ? kPerEdge : common0;
+      if (e > s && fabs(__dsub_rn(P, 1.0)) <= 1e-6) cum[e - 1] = 4294967296ull;
+      if (P > 1.0 + 1e-6) bad |= kGraphNotLT;
+    }
   }
   if (bad) atomicOr(flags, bad);
 }
@@ -64,9 +93,9 @@ cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_fla
   prep_edges_kernel<<<blocks, 256, 0, s>>>(g.n, g.m, m_pad, g.src, d_w, g.thr, d_flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int rb = (int)std::min<uint64_t>((g.n + 127) / 128, 152ull * 32);
+  int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 7) / 8, 152ull * 16);
   if (rb < 1) rb = 1;
-  prep_rows_kernel<<<rb, 128, 0, s>>>(g.n, g.off, g.src, d_w, g.cum, d_flags);
+  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, d_w, g.thr, g.rthr, g.cum, d_flags);
   return cudaGetLastError();
 }
 

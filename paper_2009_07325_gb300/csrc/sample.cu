@@ -4,12 +4,15 @@
 // from a device work counter (the role of Alg. 6's N_RR) and builds one RR
 // set at a time:
 //   IC: reverse BFS over in-edges. Frontier vertices are expanded one after
-//       another; the in-edges of a vertex are scanned by the whole warp, four
-//       consecutive edges per lane (one Philox call covers the four coins,
-//       one 16-byte load fetches four sources, one more four thresholds).
-//       A live edge whose source is not yet visited marks it in the worker's
-//       visited bitmap and appends it to the worker's queue, which doubles as
-//       the member list (Sec. III-A: each vertex is expanded once).
+//       another; the in-edges of a vertex are scanned by the whole warp, two
+//       groups of four consecutive edges per lane per step (one Philox call
+//       gives a group's four coin words). When all in-edges of the row share
+//       one probability (weighted cascade, uniform p) the row's threshold is
+//       used and the scan reads no edge data; otherwise one 16-byte load
+//       fetches the group's four thresholds. Only a live edge reads its
+//       source. A live edge whose source is not yet visited marks it in the
+//       worker's visited bitmap and appends it to the worker's queue, which
+//       doubles as the member list (Sec. III-A: each vertex expanded once).
 //   LT: the reverse walk of Sec. III-G: one draw per step, the chosen in-edge
 //       found by a 33-way warp search over the row's sorted cumulative
 //       thresholds, stop at no edge or at a vertex already on the path.
@@ -68,6 +71,29 @@ __device__ __forceinline__ void commit_set(const DevStore &st, const SampleJob &
   }
 }
 
+// Coins of group grp (in-edges 4grp .. 4grp+3) for the row [s, e): bit qi is
+// set iff edge 4grp+qi lies in the row and is live. One Philox call yields
+// the four coin words. The threshold is the row's common one when it has
+// one (rt != kPerEdge), so the scan of such a row touches no memory.
+__device__ __forceinline__ uint32_t group_live(const uint32_t *__restrict__ thr, uint32_t grp, uint32_t s, uint32_t e,
+                                               uint32_t rt, uint32_t jlo, uint32_t jhi, PhiloxKey key) {
+  const uint4 r = philox10(grp, kTagEdge, jlo, jhi, key);
+  uint4 tv;
+  if (rt != kPerEdge)
+    tv = make_uint4(rt, rt, rt, rt);
+  else
+    tv = reinterpret_cast<const uint4 *>(thr)[grp];
+  uint32_t live = ((r.x >> 8) < tv.x ? 1u : 0u) | ((r.y >> 8) < tv.y ? 2u : 0u) | ((r.z >> 8) < tv.z ? 4u : 0u) |
+                  ((r.w >> 8) < tv.w ? 8u : 0u);
+  const uint32_t e0 = grp << 2;            // s - 3 <= e0 <= e - 1
+  if (e0 < s || e0 + 4 > e) {
+    const uint32_t lo = s > e0 ? s - e0 : 0u;
+    const uint32_t hi = e - e0 < 4u ? e - e0 : 4u;
+    live &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+  }
+  return live;
+}
+
 template <bool kLarge>
 __global__ void __launch_bounds__(256) sample_ic_kernel(DevGraph g, DevStore st, WorkerScratch ws, SampleJob job,
                                                         SampleCtl *ctl) {
@@ -78,8 +104,6 @@ __global__ void __launch_bounds__(256) sample_ic_kernel(DevGraph g, DevStore st,
   uint32_t *q = ws.queue + (uint64_t)worker * ws.qcap;
   const uint32_t qcap = ws.qcap;
   const uint32_t below = (1u << lane) - 1u;
-  const uint4 *src4 = reinterpret_cast<const uint4 *>(g.src);
-  const uint4 *thr4 = reinterpret_cast<const uint4 *>(g.thr);
 
   for (;;) {
     unsigned long long item = 0;
@@ -100,31 +124,23 @@ __global__ void __launch_bounds__(256) sample_ic_kernel(DevGraph g, DevStore st,
       const uint32_t v = q[head];
       ++head;
       const uint32_t s = g.off[v], e = g.off[v + 1];
-      if (e > s) {
+      const uint32_t rt = g.rthr[v];
+      if (e > s && rt != 0u) {                  // a row whose coins are all 0 adds nothing
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
-        for (uint32_t base = g0; base <= g1; base += 32) {
-          const uint32_t grp = base + lane;
-          uint32_t live = 0;
-          uint4 sv = make_uint4(0, 0, 0, 0);
-          if (grp <= g1) {
-            sv = src4[grp];
-            const uint4 tv = thr4[grp];
-            const uint4 r = philox10(grp, kTagEdge, jlo, jhi, job.key);
-            const uint32_t e0 = grp << 2;
-            live = ((r.x >> 8) < tv.x ? 1u : 0u) | ((r.y >> 8) < tv.y ? 2u : 0u) | ((r.z >> 8) < tv.z ? 4u : 0u) |
-                   ((r.w >> 8) < tv.w ? 8u : 0u);
-            // keep only edges of this row: s <= e0 + qi < e
-            uint32_t in_row = 0;
+        for (uint32_t base = g0; base <= g1; base += 64) {
+          const uint32_t ga = base + lane, gb = base + 32 + lane;
+          uint32_t la = 0, lb = 0;
+          if (ga <= g1) la = group_live(g.thr, ga, s, e, rt, jlo, jhi, job.key);
+          if (gb <= g1) lb = group_live(g.thr, gb, s, e, rt, jlo, jhi, job.key);
+          if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
 #pragma unroll
-            for (int qi = 0; qi < 4; ++qi) in_row |= (e0 + qi >= s && e0 + qi < e) ? (1u << qi) : 0u;
-            live &= in_row;
-          }
-          if (__ballot_sync(kFullMask, live != 0) == 0) continue;
-#pragma unroll
-          for (int qi = 0; qi < 4; ++qi) {
-            const uint32_t u = comp(sv, qi);
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t grp = c < 4 ? ga : gb;
+            const bool cand = (((c < 4 ? la : lb) >> (c & 3)) & 1u) != 0u;
+            uint32_t u = 0;
             bool fresh = false;
-            if ((live >> qi) & 1u) {
+            if (cand) {
+              u = g.src[(grp << 2) + (c & 3)];   // only live edges read their source
               const uint32_t bit = 1u << (u & 31u);
               fresh = (atomicOr(&bm[u >> 5], bit) & bit) == 0u;
             }
@@ -270,7 +286,27 @@ __global__ void uncount_kernel(DevStore st, uint64_t j_begin, uint64_t count) {
   }
 }
 
+// Pure Philox4x32-10 throughput: each thread draws `per_thread` blocks on
+// consecutive counters (the IC coin counter layout) and folds the words so
+// that nothing is optimised away. Measures the ALU ceiling of the coin work.
+__global__ void __launch_bounds__(256) philox_rate_kernel(PhiloxKey key, uint32_t per_thread, uint32_t *sink) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (uint32_t i = 0; i < per_thread; i += 2) {
+    const uint32_t c = t * per_thread + i;
+    const uint4 a = philox10(c, kTagEdge, 0x1234u, 0u, key);
+    const uint4 b = philox10(c + 1, kTagEdge, 0x1234u, 0u, key);
+    acc += (a.x ^ a.y ^ a.z ^ a.w) + (b.x ^ b.y ^ b.z ^ b.w);
+  }
+  if (acc == 0x9E3779B9u) sink[t & 1023] = acc;   // practically never stored
+}
+
 }  // namespace
+
+cudaError_t launch_philox_rate(int blocks, uint32_t per_thread, uint32_t *sink, cudaStream_t s) {
+  philox_rate_kernel<<<blocks, 256, 0, s>>>(PhiloxKey{0x01234567u, 0x89ABCDEFu}, per_thread, sink);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sample(int model, const DevGraph &g, const DevStore &st, const WorkerScratch &ws, const SampleJob &job,
                           SampleCtl *ctl, bool large, int grid, int block, cudaStream_t s) {
