@@ -138,6 +138,47 @@ gim_status gim_select_seeds(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint6
 gim_status gim_imm(gim_ctx *ctx, gim_model model, uint32_t k, double eps, double ell, uint64_t seed,
                    uint32_t *seeds_out, uint64_t *theta_out, double *lb_out);
 
+/*
+ * Greedy maximum coverage that allocates no memory. The paper has no
+ * counterpart: this entry point exists for callers that cannot let a
+ * library allocate device memory - processes whose device memory is
+ * reserved up front by their own pool or arena, where a foreign cudaMalloc
+ * would fail or break their budget, and latency-critical paths that cannot
+ * afford the synchronisation an allocation may bring. It computes exactly
+ * what gim_select_seeds computes (same kernels, same tie rule), over an RR
+ * collection the caller holds in device memory, and needs no context.
+ *   n:             number of vertices, 1 <= n <= 65536.
+ *   num_sets:      number of RR sets R, <= 262144.
+ *   num_members:   total members Z = d_rr_offsets[R], <= 1048576.
+ *   d_rr_offsets:  DEVICE pointer, R+1 entries: set j is
+ *                  d_rr_members[d_rr_offsets[j] .. d_rr_offsets[j+1]).
+ *   d_rr_members:  DEVICE pointer, Z vertex ids < n (a set lists each
+ *                  vertex at most once).
+ *   k:             1 <= k <= min(n, 1024).
+ *   d_seeds_out:   DEVICE pointer, k entries (required).
+ *   d_gains_out:   DEVICE pointer, k entries, nullable.
+ *   d_covered_out: DEVICE pointer, one uint64, nullable.
+ *   stream:        cudaStream_t of the current device (NULL: legacy default).
+ *   msg, msg_len:  nullable caller buffer for an error description.
+ * Scratch: one fixed array of about 6.6 MB in the library's device image,
+ * present on every device that loads the library until the process exits.
+ * The first call on a device looks up the array's device address (set-up,
+ * done once per device under a lock); make that first call before any stream
+ * capture begins. Every call on a device shares the array and finds it as
+ * the previous call left it (the call clears what must start at zero), so
+ * calls whose work overlaps on the GPU - concurrent streams, or concurrent
+ * host threads on one device - race and must be serialised by the caller.
+ * The call synchronises `stream` twice to validate its inputs and returns
+ * with the greedy rounds enqueued on `stream`.
+ * Errors: GIM_ERR_ARG (a size above the limits, k > n, a null required
+ * pointer, offsets not starting at 0 / decreasing / not ending at
+ * num_members, a member >= n), GIM_ERR_CUDA.
+ */
+gim_status gim_select_seeds_noalloc(uint32_t n, uint64_t num_sets, uint64_t num_members,
+                                    const uint64_t *d_rr_offsets, const uint32_t *d_rr_members, uint32_t k,
+                                    uint32_t *d_seeds_out, uint32_t *d_gains_out, uint64_t *d_covered_out,
+                                    void *stream, char *msg, size_t msg_len);
+
 /* ---- introspection (tests, tools) ------------------------------------- */
 
 /* *count_out = |R|; *members_out (nullable) = total members over all sets. */

@@ -48,6 +48,9 @@ SIGNATURES = {
     "gim_diag_philox_rate": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_launch_count": (ctypes.c_int, [_vp, _c_u64p]),
     "gim_last_error_string": (ctypes.c_char_p, [_vp]),
+    "gim_select_seeds_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp,
+                                                ctypes.c_uint32, _vp, _vp, _vp, _vp, ctypes.c_char_p,
+                                                ctypes.c_size_t]),
 }
 
 
@@ -194,3 +197,19 @@ class Context:
         c = ctypes.c_uint64(0)
         self._check(self.L.gim_launch_count(self.h, ctypes.byref(c)), "gim_launch_count")
         return int(c.value)
+
+
+def select_seeds_noalloc(n: int, num_sets: int, num_members: int, d_offsets: int, d_members: int, k: int,
+                         d_seeds: int, d_gains: int = 0, d_covered: int = 0, stream: int = 0) -> None:
+    """gim_select_seeds_noalloc on caller-owned device buffers (raw device addresses).
+
+    For callers that cannot let the library allocate device memory; see the
+    declaration in include/gim.h for limits and the shared-scratch contract.
+    """
+    L = load_library()
+    buf = ctypes.create_string_buffer(256)
+    st = L.gim_select_seeds_noalloc(n, num_sets, num_members, _vp(d_offsets), _vp(d_members), k, _vp(d_seeds),
+                                    _vp(d_gains) if d_gains else None, _vp(d_covered) if d_covered else None,
+                                    _vp(stream) if stream else None, buf, 256)
+    if st != 0:
+        raise GimError(st, "gim_select_seeds_noalloc: " + buf.value.decode())

@@ -12,6 +12,9 @@
 //           flagged covered and the counts of its members are lowered.
 // Counts are kept as count + 1 for unselected vertices and 0 once selected.
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
 
 #include "gim_internal.cuh"
 
@@ -223,6 +226,44 @@ __global__ void __launch_bounds__(256) cover_kernel(uint32_t t, DevStore st, con
   }
 }
 
+// Checks a caller-given RR collection in CSR form: offsets non-decreasing,
+// offsets[0] = 0 and offsets[R] = Z. Sets bit 1 of *flags otherwise.
+__global__ void __launch_bounds__(256) na_check_offsets_kernel(const uint64_t *__restrict__ off, uint64_t R,
+                                                               uint64_t Z, unsigned int *__restrict__ flags) {
+  bool bad = false;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j <= R; j += (uint64_t)gridDim.x * blockDim.x) {
+    if (j == 0 && off[0] != 0) bad = true;
+    if (j == R && off[R] != Z) bad = true;
+    if (j < R && off[j + 1] < off[j]) bad = true;
+  }
+  if (bad) atomicOr(flags, 1u);
+}
+
+// Set lengths and occurrence counts of a caller-given collection (counts must
+// be zero on entry). A member id >= n sets bit 2 of *flags and is skipped.
+__global__ void __launch_bounds__(256) na_lengths_counts_kernel(const uint64_t *__restrict__ off,
+                                                                const uint32_t *__restrict__ members, uint64_t R,
+                                                                uint32_t n, uint32_t *__restrict__ len,
+                                                                uint32_t *__restrict__ cnt,
+                                                                unsigned int *__restrict__ flags) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  bool bad = false;
+  for (uint64_t j = warp; j < R; j += nwarps) {
+    const uint64_t b = off[j], e = off[j + 1];
+    if (lane == 0) len[j] = (uint32_t)(e - b);
+    for (uint64_t t = b + lane; t < e; t += 32) {
+      const uint32_t x = members[t];
+      if (x < n)
+        atomicAdd(&cnt[x], 1u);
+      else
+        bad = true;
+    }
+  }
+  if (bad) atomicOr(flags, 2u);
+}
+
 template <typename T>
 cudaError_t ensure(T *&p, uint64_t &cap, uint64_t need) {
   if (need <= cap && p) return cudaSuccess;
@@ -295,3 +336,181 @@ cudaError_t run_select(const DevGraph &g, const DevStore &st, uint64_t R, uint64
 }
 
 }  // namespace gim
+
+// ===========================================================================
+// Allocation-free greedy selection (gim_select_seeds_noalloc in gim.h).
+//
+// Some callers cannot let a library call cudaMalloc/cudaFree: processes whose
+// device memory is fully reserved up front by their own pool or arena (so a
+// foreign allocation would fail or break their budget), and latency-critical
+// paths that cannot afford the synchronisation an allocation may imply. For
+// them this entry point runs the same selection kernels as gim_select_seeds
+// with every scratch buffer carved out of one fixed-size array that lives in
+// the library's device image. Callers pass their inputs and outputs in device
+// memory they own.
+// ===========================================================================
+namespace {
+
+constexpr uint64_t na_align(uint64_t x) { return (x + 255) / 256 * 256; }
+
+constexpr uint32_t kNaMaxN = 1u << 16;            // vertices
+constexpr uint64_t kNaMaxSets = 1ull << 18;       // RR sets
+constexpr uint64_t kNaMaxMembers = 1ull << 20;    // members over all sets
+constexpr uint32_t kNaMaxK = 1024;                // seeds
+constexpr uint64_t kNaTiles = (kNaMaxN + gim::kScanTile - 1) / gim::kScanTile;
+
+constexpr uint64_t kNaCnt = 0;
+constexpr uint64_t kNaCntWork = kNaCnt + na_align(4ull * (kNaMaxN + 4));
+constexpr uint64_t kNaInvOff = kNaCntWork + na_align(4ull * (kNaMaxN + 4));
+constexpr uint64_t kNaCursor = kNaInvOff + na_align(8ull * (kNaMaxN + 4));
+constexpr uint64_t kNaInv = kNaCursor + na_align(4ull * (kNaMaxN + 4));
+constexpr uint64_t kNaCovered = kNaInv + na_align(4ull * kNaMaxMembers);
+constexpr uint64_t kNaLen = kNaCovered + na_align(kNaMaxSets);
+constexpr uint64_t kNaBest = kNaLen + na_align(4ull * kNaMaxSets);
+constexpr uint64_t kNaGains = kNaBest + na_align(8ull * kNaMaxK);
+constexpr uint64_t kNaTotal = kNaGains + na_align(4ull * kNaMaxK);
+constexpr uint64_t kNaScan = kNaTotal + 256;
+constexpr uint64_t kNaFlags = kNaScan + na_align(8ull * (kNaTiles + 1));
+constexpr uint64_t kNaBytes = kNaFlags + 256;     // about 6.6 MB
+
+}  // namespace
+
+// The scratch of gim_select_seeds_noalloc: loaded with the library on every
+// device that uses it and kept until the process exits.
+static __device__ __align__(256) unsigned char gim_noalloc_scratch[kNaBytes];
+
+namespace {
+
+std::mutex g_na_mutex;
+unsigned char *g_na_ptr[256] = {};   // device address of the scratch, per device ordinal
+
+void na_msg(char *msg, size_t msg_len, const char *text) {
+  if (msg && msg_len) {
+    std::strncpy(msg, text, msg_len - 1);
+    msg[msg_len - 1] = '\0';
+  }
+}
+
+}  // namespace
+
+extern "C" gim_status gim_select_seeds_noalloc(uint32_t n, uint64_t num_sets, uint64_t num_members,
+                                               const uint64_t *d_rr_offsets, const uint32_t *d_rr_members,
+                                               uint32_t k, uint32_t *d_seeds_out, uint32_t *d_gains_out,
+                                               uint64_t *d_covered_out, void *stream, char *msg, size_t msg_len) {
+  using namespace gim;
+  na_msg(msg, msg_len, "");
+  if (n < 1 || n > kNaMaxN || num_sets > kNaMaxSets || num_members > kNaMaxMembers || k < 1 || k > kNaMaxK ||
+      k > n) {
+    char buf[256];
+    std::snprintf(buf, sizeof buf,
+                  "size above the limit: need 1 <= n <= %u, sets <= %llu, members <= %llu, 1 <= k <= min(n, %u)",
+                  kNaMaxN, (unsigned long long)kNaMaxSets, (unsigned long long)kNaMaxMembers, kNaMaxK);
+    na_msg(msg, msg_len, buf);
+    return GIM_ERR_ARG;
+  }
+  if (!d_rr_offsets || (num_members && !d_rr_members) || !d_seeds_out) {
+    na_msg(msg, msg_len, "null input or output pointer");
+    return GIM_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    na_msg(msg, msg_len, "no usable current CUDA device");
+    return GIM_ERR_CUDA;
+  }
+  unsigned char *base = nullptr;
+  {
+    // set-up, once per device, with that device current: the host-side name
+    // of the array is not a device address, so ask the runtime for it
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+      void *p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, gim_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        na_msg(msg, msg_len, "cudaGetSymbolAddress of the selection scratch failed");
+        return GIM_ERR_CUDA;
+      }
+      g_na_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    base = g_na_ptr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(base + kNaCnt);
+  uint32_t *cnt_work = reinterpret_cast<uint32_t *>(base + kNaCntWork);
+  uint64_t *inv_off = reinterpret_cast<uint64_t *>(base + kNaInvOff);
+  uint32_t *cursor = reinterpret_cast<uint32_t *>(base + kNaCursor);
+  uint32_t *inv = reinterpret_cast<uint32_t *>(base + kNaInv);
+  uint8_t *covered = base + kNaCovered;
+  uint32_t *len = reinterpret_cast<uint32_t *>(base + kNaLen);
+  unsigned long long *best = reinterpret_cast<unsigned long long *>(base + kNaBest);
+  uint32_t *gains = d_gains_out ? d_gains_out : reinterpret_cast<uint32_t *>(base + kNaGains);
+  unsigned long long *total = reinterpret_cast<unsigned long long *>(base + kNaTotal);
+  uint64_t *scan_tmp = reinterpret_cast<uint64_t *>(base + kNaScan);
+  unsigned int *flags = reinterpret_cast<unsigned int *>(base + kNaFlags);
+
+  auto fail = [&](cudaError_t e, const char *what) {
+    cudaGetLastError();
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    na_msg(msg, msg_len, buf);
+    return e == cudaErrorMemoryAllocation ? GIM_ERR_OOM : GIM_ERR_CUDA;
+  };
+  cudaError_t e;
+  unsigned int hflags = 0;
+  // everything that must start at zero is cleared here: the array keeps the
+  // previous call's contents
+  if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return fail(e, "clear flags");
+  if ((e = cudaMemsetAsync(cnt, 0, 4ull * n, s)) != cudaSuccess) return fail(e, "clear counts");
+  const unsigned ob = (unsigned)std::min<uint64_t>((num_sets + 256) / 256, 1024);
+  na_check_offsets_kernel<<<ob, 256, 0, s>>>(d_rr_offsets, num_sets, num_members, flags);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "offset check");
+  if ((e = cudaMemcpyAsync(&hflags, flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(e, "flags");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "offset check");
+  if (hflags) {
+    na_msg(msg, msg_len, "rr offsets must start at 0, not decrease and end at num_members");
+    return GIM_ERR_ARG;
+  }
+  if (num_sets) {
+    const unsigned lb = (unsigned)std::min<uint64_t>((num_sets + 7) / 8, 2048);
+    na_lengths_counts_kernel<<<lb, 256, 0, s>>>(d_rr_offsets, d_rr_members, num_sets, n, len, cnt, flags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "counts");
+    if ((e = cudaMemcpyAsync(&hflags, flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(e, "flags");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "counts");
+    if (hflags) {
+      na_msg(msg, msg_len, "a member id is >= n");
+      return GIM_ERR_ARG;
+    }
+  }
+  DevStore st;
+  st.members = const_cast<uint32_t *>(d_rr_members);
+  st.rr_start = const_cast<uint64_t *>(d_rr_offsets);   // set j starts at offsets[j]
+  st.rr_len = len;
+  st.cnt = cnt;
+  st.cap = num_members;
+  const uint64_t tiles = ((uint64_t)n + kScanTile - 1) / kScanTile;
+  scan_tiles_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(cnt, n, scan_tmp);
+  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, tiles);
+  scan_apply_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(cnt, n, scan_tmp, inv_off, cnt_work, cursor);
+  if (num_sets) {
+    const unsigned fb = (unsigned)std::min<uint64_t>((num_sets + 7) / 8, 2048);
+    fill_inv_kernel<<<fb, 256, 0, s>>>(st, num_sets, inv_off, cursor, inv);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "inverted index");
+  if ((e = cudaMemsetAsync(covered, 0, std::max<uint64_t>(num_sets, 1), s)) != cudaSuccess) return fail(e, "clear");
+  if ((e = cudaMemsetAsync(best, 0, 8ull * k, s)) != cudaSuccess) return fail(e, "clear");
+  if ((e = cudaMemsetAsync(total, 0, 8, s)) != cudaSuccess) return fail(e, "clear");
+  int sm = 0;
+  if ((e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return fail(e, "sm count");
+  const unsigned am = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)n / 4 + 255) / 256, 4ull * sm));
+  for (uint32_t t = 0; t < k; ++t) {
+    argmax_kernel<<<am, 256, 0, s>>>(cnt_work, n, best + t);
+    cover_kernel<<<(unsigned)sm * 8, 256, 0, s>>>(t, st, best, cnt_work, inv_off, inv, covered, d_seeds_out, gains,
+                                                   total);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "greedy rounds");
+  if (d_covered_out &&
+      (e = cudaMemcpyAsync(d_covered_out, total, 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return fail(e, "covered count");
+  return GIM_OK;
+}
