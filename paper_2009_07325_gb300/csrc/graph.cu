@@ -29,14 +29,49 @@ __global__ void prep_edges_kernel(uint32_t n, uint64_t m, uint64_t m_pad, const 
   if (bad) atomicOr(flags, bad);
 }
 
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(kFullMask, v, d);
+    if (lane >= (uint32_t)d) v += o;
+  }
+  return v;
+}
+
+// fp32 weight w = M * 2^E exactly (M < 2^24); returns E, or INT_MAX for w = 0.
+__device__ __forceinline__ int ulp_exponent(float w, uint32_t *mant) {
+  const uint32_t b = __float_as_uint(w);
+  const uint32_t ef = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (ef == 0 && m == 0) {
+    *mant = 0;
+    return 0x7FFFFFFF;
+  }
+  *mant = ef ? (m | 0x800000u) : m;
+  return ef ? (int)ef - 150 : -149;
+}
+
+__device__ __forceinline__ unsigned long long lt_round(double P) {
+  const double x = __dmul_rn(P, 4294967296.0);
+  const double f = floor(x);
+  unsigned long long c = (unsigned long long)f;
+  if (__dsub_rn(x, f) >= 0.5) c += 1ull;
+  return c > 4294967296ull ? 4294967296ull : c;
+}
+
 // Warp per row: ascending sources within the row, the row's common IC
-// threshold (rthr), and the LT thresholds.
-// cum[e_i] = min(2^32, round_half_up(P_i * 2^32)), P_i the fp64 running sum of
-// the row's weights in CSR order; a row summing to within 1e-6 of 1 gets
-// cum[last] = 2^32 so that it always selects an edge. A row summing above
-// 1 + 1e-6 marks the graph as not valid for LT. The loads are coalesced; the
-// running sum stays strictly sequential (every lane adds the 32 broadcast
-// weights of a chunk in order and keeps the prefix that ends at its edge).
+// threshold (rthr), and the LT thresholds
+//   cum[e_i] = min(2^32, round_half_up(P_i * 2^32)),
+// P_i the fp64 running sum of the row's weights in CSR order; a row summing
+// to within 1e-6 of 1 gets cum[last] = 2^32 so that it always selects an
+// edge, and a row summing above 1 + 1e-6 marks the graph as not valid for LT.
+// The running sum is computed exactly: with E the smallest ulp exponent of
+// the row's non-zero weights, every weight is an integer q_t times 2^E; when
+// all prefix sums of the q_t stay below 2^53, every fp64 partial sum is
+// representable, so the sequential fp64 additions never round and P_i equals
+// the integer prefix sum times 2^E, which the warp computes with a parallel
+// scan. Other rows (weights spanning more than 2^39, or huge sums) take the
+// strictly sequential fp64 loop. Both give the same P_i.
 __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off,
                                                         const uint32_t *__restrict__ src,
                                                         const float *__restrict__ w,
@@ -51,29 +86,71 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
     const uint32_t s = off[v], e = off[v + 1];
     const uint32_t common0 = e > s ? thr[s] : 0u;
     bool differs = false;
-    double P = 0.0;
+    int emin = 0x7FFFFFFF;
+    // pass 1: checks, smallest ulp exponent
     for (uint32_t base = s; base < e; base += 32) {
       const uint32_t i = base + lane;
       const bool in = i < e;
-      const float wi = in ? w[i] : 0.0f;
       const uint32_t si = in ? src[i] : 0u;
       if (in && thr[i] != common0) differs = true;
       uint32_t prev = __shfl_up_sync(kFullMask, si, 1);
       if (lane == 0 && base > s) prev = src[base - 1];
       if (in && i > s && !(prev < si)) bad |= kGraphNotAscending;
-      const uint32_t cnt = e - base < 32u ? e - base : 32u;
-      double mine = 0.0;
-      for (uint32_t t = 0; t < cnt; ++t) {
-        P = __dadd_rn(P, (double)__shfl_sync(kFullMask, wi, t));
-        if (t == lane) mine = P;
+      uint32_t mant;
+      const int ex = in ? ulp_exponent(w[i], &mant) : 0x7FFFFFFF;
+      emin = min(emin, ex);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) emin = min(emin, __shfl_xor_sync(kFullMask, emin, d));
+    // pass 2: exact parallel prefix sums when no fp64 addition can round
+    bool exact = true;
+    unsigned long long carry = 0;
+    double scale = 1.0;
+    if (emin == 0x7FFFFFFF) {
+      for (uint32_t i = s + lane; i < e; i += 32) cum[i] = 0ull;      // all weights zero
+    } else {
+      scale = __longlong_as_double((long long)(emin + 1023) << 52);   // 2^emin, emin >= -149
+      for (uint32_t base = s; base < e && exact; base += 32) {
+        const uint32_t i = base + lane;
+        unsigned long long q = 0;
+        bool ok = true;
+        if (i < e) {
+          uint32_t mant;
+          const int ex = ulp_exponent(w[i], &mant);
+          if (ex != 0x7FFFFFFF) {
+            const int sh = ex - emin;
+            if (sh > 29) ok = false;                      // q would reach 2^53
+            else q = (unsigned long long)mant << sh;
+          }
+        }
+        if (!__all_sync(kFullMask, ok)) {
+          exact = false;
+          break;
+        }
+        const unsigned long long incl = warp_incl_scan_u64(q) + carry;
+        carry = __shfl_sync(kFullMask, incl, 31);
+        if (carry >= (1ull << 53)) {
+          exact = false;
+          break;
+        }
+        if (i < e) cum[i] = lt_round(__dmul_rn(__ull2double_rn(incl), scale));
       }
-      if (in) {
-        const double x = __dmul_rn(mine, 4294967296.0);
-        const double f = floor(x);
-        unsigned long long c = (unsigned long long)f;
-        if (__dsub_rn(x, f) >= 0.5) c += 1ull;
-        if (c > 4294967296ull) c = 4294967296ull;
-        cum[i] = c;
+    }
+    double P = 0.0;
+    if (exact) {
+      P = __dmul_rn(__ull2double_rn(carry), scale);
+    } else {
+      // sequential fp64: every lane adds the broadcast weights in CSR order
+      for (uint32_t base = s; base < e; base += 32) {
+        const uint32_t i = base + lane;
+        const float wi = i < e ? w[i] : 0.0f;
+        const uint32_t cnt = e - base < 32u ? e - base : 32u;
+        double mine = 0.0;
+        for (uint32_t t = 0; t < cnt; ++t) {
+          P = __dadd_rn(P, (double)__shfl_sync(kFullMask, wi, t));
+          if (t == lane) mine = P;
+        }
+        if (i < e) cum[i] = lt_round(mine);
       }
     }
     const bool any_diff = __any_sync(kFullMask, differs);

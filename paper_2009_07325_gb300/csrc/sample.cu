@@ -3,16 +3,18 @@
 // A persistent grid of warps; each warp is one worker that takes RR-set ids
 // from a device work counter (the role of Alg. 6's N_RR) and builds one RR
 // set at a time:
-//   IC: reverse BFS over in-edges. Frontier vertices are expanded one after
-//       another; the in-edges of a vertex are scanned by the whole warp, two
-//       groups of four consecutive edges per lane per step (one Philox call
-//       gives a group's four coin words). When all in-edges of the row share
-//       one probability (weighted cascade, uniform p) the row's threshold is
-//       used and the scan reads no edge data; otherwise one 16-byte load
-//       fetches the group's four thresholds. Only a live edge reads its
-//       source. A live edge whose source is not yet visited marks it in the
-//       worker's visited bitmap and appends it to the worker's queue, which
-//       doubles as the member list (Sec. III-A: each vertex expanded once).
+//   IC: reverse BFS over in-edges. Frontier vertices are taken in batches of
+//       up to 32, whose queue entries, offsets and row thresholds are loaded
+//       in one round trip; the rows are then scanned one after another by the
+//       whole warp, two groups of four consecutive edges per lane per step
+//       (one Philox call gives a group's four coin words). When all in-edges
+//       of a row share one probability (weighted cascade, uniform p) the
+//       row's threshold is used and the scan reads no edge data; otherwise
+//       one 16-byte load fetches the group's four thresholds. Live edges are
+//       buffered in shared memory; the buffer is resolved 32 edges at a time
+//       (read the source, test-and-set its bit in the worker's visited bitmap,
+//       append the newly visited to the worker's queue, which doubles as the
+//       member list: Sec. III-A, each vertex is expanded once).
 //   LT: the reverse walk of Sec. III-G: one draw per step, the chosen in-edge
 //       found by a 33-way warp search over the row's sorted cumulative
 //       thresholds, stop at no edge or at a vertex already on the path.
@@ -94,16 +96,55 @@ __device__ __forceinline__ uint32_t group_live(const uint32_t *__restrict__ thr,
   return live;
 }
 
+constexpr uint32_t kCandCap = 512;   // per-warp buffer of live edges awaiting their visited test
+
+// Resolves the buffered live edges cand[0..ncand): reads each one's source,
+// test-and-sets its visited bit and appends the newly visited sources to the
+// queue (32 edges per round trip). Lane-uniform control.
+__device__ __forceinline__ void ic_flush(const uint32_t *__restrict__ src, const uint32_t *cand, uint32_t ncand,
+                                         uint32_t *bm, uint32_t *q, uint32_t qcap, uint32_t &tail, bool &overflow) {
+  const uint32_t lane = lane_id();
+  const uint32_t below = (1u << lane) - 1u;
+  __syncwarp();
+  for (uint32_t i0 = 0; i0 < ncand; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    uint32_t u = 0;
+    bool fresh = false;
+    if (i < ncand) {
+      u = src[cand[i]];
+      const uint32_t bit = 1u << (u & 31u);
+      fresh = (atomicOr(&bm[u >> 5], bit) & bit) == 0u;
+    }
+    const uint32_t fm = __ballot_sync(kFullMask, fresh);
+    if (fm) {
+      const uint32_t pos = tail + __popc(fm & below);
+      if (fresh) {
+        if (pos < qcap)
+          q[pos] = u;
+        else
+          atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));   // not queued: leave no trace
+      }
+      tail += __popc(fm);
+      if (tail > qcap) {
+        tail = qcap;
+        overflow = true;
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <bool kLarge>
 __global__ void __launch_bounds__(256) sample_ic_kernel(DevGraph g, DevStore st, WorkerScratch ws, SampleJob job,
                                                         SampleCtl *ctl) {
+  __shared__ uint32_t cand_all[8][kCandCap];
   const uint32_t lane = lane_id();
   const uint32_t worker = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (worker >= ws.workers) return;
+  uint32_t *cand = cand_all[threadIdx.x >> 5];
   uint32_t *bm = ws.bitmap + (uint64_t)worker * ws.words_per_worker;
   uint32_t *q = ws.queue + (uint64_t)worker * ws.qcap;
   const uint32_t qcap = ws.qcap;
-  const uint32_t below = (1u << lane) - 1u;
 
   for (;;) {
     unsigned long long item = 0;
@@ -117,54 +158,55 @@ __global__ void __launch_bounds__(256) sample_ic_kernel(DevGraph g, DevStore st,
       q[0] = root;
       bm[root >> 5] = 1u << (root & 31u);   // the worker's bitmap is all zero here
     }
-    __syncwarp();
     uint32_t head = 0, tail = 1;
     bool overflow = false;
-    while (head < tail) {
-      const uint32_t v = q[head];
-      ++head;
-      const uint32_t s = g.off[v], e = g.off[v + 1];
-      const uint32_t rt = g.rthr[v];
-      if (e > s && rt != 0u) {                  // a row whose coins are all 0 adds nothing
+    while (head < tail && !overflow) {
+      __syncwarp();
+      // a batch of up to 32 frontier vertices: their rows are fetched at once
+      const uint32_t nb = tail - head < 32u ? tail - head : 32u;
+      uint32_t rs = 0, re = 0, rr = 0;
+      if (lane < nb) {
+        const uint32_t v = q[head + lane];
+        rs = g.off[v];
+        re = g.off[v + 1];
+        rr = g.rthr[v];
+      }
+      head += nb;
+      uint32_t ncand = 0;
+      for (uint32_t b = 0; b < nb && !overflow; ++b) {
+        const uint32_t s = __shfl_sync(kFullMask, rs, b), e = __shfl_sync(kFullMask, re, b);
+        const uint32_t rt = __shfl_sync(kFullMask, rr, b);
+        if (e <= s || rt == 0u) continue;      // a row whose coins are all 0 adds nothing
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
         for (uint32_t base = g0; base <= g1; base += 64) {
           const uint32_t ga = base + lane, gb = base + 32 + lane;
           uint32_t la = 0, lb = 0;
           if (ga <= g1) la = group_live(g.thr, ga, s, e, rt, jlo, jhi, job.key);
           if (gb <= g1) lb = group_live(g.thr, gb, s, e, rt, jlo, jhi, job.key);
-          if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
+          const uint32_t mine = __popc(la) + __popc(lb);
+          if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
+          uint32_t incl = mine;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint32_t grp = c < 4 ? ga : gb;
-            const bool cand = (((c < 4 ? la : lb) >> (c & 3)) & 1u) != 0u;
-            uint32_t u = 0;
-            bool fresh = false;
-            if (cand) {
-              u = g.src[(grp << 2) + (c & 3)];   // only live edges read their source
-              const uint32_t bit = 1u << (u & 31u);
-              fresh = (atomicOr(&bm[u >> 5], bit) & bit) == 0u;
-            }
-            const uint32_t fm = __ballot_sync(kFullMask, fresh);
-            if (fm) {
-              const uint32_t pos = tail + __popc(fm & below);
-              if (fresh) {
-                if (pos < qcap)
-                  q[pos] = u;
-                else
-                  atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));   // not queued: leave no trace
-              }
-              tail += __popc(fm);
-              if (tail > qcap) {
-                tail = qcap;
-                overflow = true;
-              }
-            }
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(kFullMask, incl, d);
+            if (lane >= (uint32_t)d) incl += o;
           }
-          if (overflow) break;
+          const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+          if (ncand + total > kCandCap) {
+            ic_flush(g.src, cand, ncand, bm, q, qcap, tail, overflow);
+            ncand = 0;
+          }
+          uint32_t pos = ncand + incl - mine;
+#pragma unroll
+          for (int qi = 0; qi < 4; ++qi)
+            if ((la >> qi) & 1u) cand[pos++] = (ga << 2) + qi;
+#pragma unroll
+          for (int qi = 0; qi < 4; ++qi)
+            if ((lb >> qi) & 1u) cand[pos++] = (gb << 2) + qi;
+          ncand += total;
         }
       }
-      __syncwarp();
-      if (overflow) break;
+      ic_flush(g.src, cand, ncand, bm, q, qcap, tail, overflow);
     }
     if (overflow) {
       for (uint32_t i = lane; i < tail; i += 32) bm[q[i] >> 5] = 0u;

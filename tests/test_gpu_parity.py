@@ -123,6 +123,37 @@ def test_rmat22_ic_p001_giant_sets_bit_exact(rmat22):
     assert gs.tolist() == os_.tolist() and gg.tolist() == og.tolist() and gc == oc
 
 
+def test_lt_thresholds_exact_and_sequential_rows_bit_exact():
+    """LT thresholds: rows whose fp64 prefix sums are exact (parallel path), rows
+    whose weights span more than 2^39 (sequential fp64 path), zero weights."""
+    base = I.er(3000, 24000, 17)
+    rng = np.random.default_rng(5)
+    d = base.indegree()
+    w = np.zeros(base.m, np.float64)
+    off = base.offsets.astype(np.int64)
+    for v in range(base.n):
+        row = slice(off[v], off[v + 1])
+        kind = v % 4
+        if kind == 0:      # weighted cascade
+            w[row] = 1.0 / max(d[v], 1)
+        elif kind == 1:    # random, scaled to sum 0.9
+            x = rng.random(d[v])
+            w[row] = 0.9 * x / max(x.sum(), 1e-300)
+        elif kind == 2:    # tiny and large weights in one row: fp64 sums round
+            x = np.where(rng.random(d[v]) < 0.5, 1e-30, rng.random(d[v]) * 0.2)
+            w[row] = x * (0.95 / max(x.sum(), 1e-300))
+        else:              # zero weights mixed in, or an all-zero row
+            x = np.where(rng.random(d[v]) < 0.4, 0.0, rng.random(d[v]))
+            w[row] = (0.0 if v % 8 == 3 else 0.7) * x / max(x.sum(), 1e-300)
+    g = base.with_weights(w.astype(np.float32), "mixed")
+    ctx = _ctx(g)
+    orc = O.Oracle(g)
+    assert ctx.lt_valid and orc.lt_valid
+    ctx.sample_rr(GIM_LT, 30000, 21)
+    orc.sample(GIM_LT, 21, 30000, THREADS)
+    _same_collection(ctx, orc)
+
+
 def test_store_growth_and_large_sets():
     """p = 1 on a strongly connected ER graph: every RR set is ~n vertices, so each
     set overflows the worker queue and the store (64M entries) must grow."""
