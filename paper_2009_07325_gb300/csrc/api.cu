@@ -14,29 +14,6 @@ using namespace gim;
 
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kWarpsPerBlock = kBlock / 32;
-constexpr uint32_t kIcQueueCap = 4096;        // per-worker queue of the common-case IC pass
-constexpr uint32_t kLtPathCap = 1024;         // per-warp shared-memory path of the common-case LT pass
-constexpr uint64_t kScratchBudget = 4ull << 30;   // bytes of visited bitmaps + queues per pass
-constexpr uint64_t kInitialStore = 1ull << 26;    // store entries at first use
-
-gim_status set_err(gim_ctx *ctx, gim_status st, const char *fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  if (ctx) ctx->last_error = buf;
-  return st;
-}
-
-gim_status cuda_err(gim_ctx *ctx, cudaError_t e, const char *what) {
-  cudaGetLastError();   // clear a non-sticky error so the context stays usable
-  if (e == cudaErrorMemoryAllocation) return set_err(ctx, GIM_ERR_OOM, "%s: out of device memory", what);
-  return set_err(ctx, GIM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
 #define CU(call)                                              \
   do {                                                        \
     cudaError_t e_ = (call);                                  \
@@ -58,12 +35,6 @@ void free_graph(DevGraph &g) {
   g = DevGraph{};
 }
 
-void free_scratch(WorkerScratch &w) {
-  dfree(w.bitmap);
-  dfree(w.queue);
-  w = WorkerScratch{};
-}
-
 void free_select(SelectBuffers &b) {
   dfree(b.cnt_work);
   dfree(b.inv_off);
@@ -78,174 +49,14 @@ void free_select(SelectBuffers &b) {
   b = SelectBuffers{};
 }
 
-// Allocates zeroed per-worker scratch: `workers` workers, each with a visited
-// bitmap of n bits and a queue of qcap entries (either may be skipped).
-cudaError_t alloc_scratch(WorkerScratch &w, uint32_t n, uint32_t workers, uint32_t qcap, bool bitmap, bool queue,
-                          cudaStream_t s) {
-  free_scratch(w);
-  w.workers = workers;
-  w.qcap = qcap;
-  w.words_per_worker = bitmap ? ((uint64_t)n + 31) / 32 : 0;
-  w.words_per_worker = (w.words_per_worker + 31) / 32 * 32;   // 128-byte aligned per worker
-  cudaError_t e;
-  if (bitmap) {
-    if ((e = cudaMalloc(&w.bitmap, w.words_per_worker * workers * 4)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.bitmap, 0, w.words_per_worker * workers * 4, s)) != cudaSuccess) return e;
-  }
-  if (queue) {
-    if ((e = cudaMalloc(&w.queue, (uint64_t)qcap * workers * 4)) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-uint32_t cap_workers(uint64_t per_worker_bytes, uint32_t want) {
-  const uint64_t lim = std::max<uint64_t>(kWarpsPerBlock, kScratchBudget / std::max<uint64_t>(per_worker_bytes, 1));
-  uint64_t w = std::min<uint64_t>(want, lim);
-  w = w / kWarpsPerBlock * kWarpsPerBlock;
-  return (uint32_t)std::max<uint64_t>(w, kWarpsPerBlock);
-}
-
-template <typename T>
-cudaError_t grow_copy(T *&p, uint64_t &cap, uint64_t need, uint64_t keep, cudaStream_t s) {
-  if (need <= cap && p) return cudaSuccess;
-  const uint64_t c = std::max<uint64_t>(need, cap * 2);
-  T *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, c * sizeof(T));
-  if (e != cudaSuccess) return e;
-  if (p && keep) {
-    e = cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) {
-      cudaFree(q);
-      return e;
-    }
-  }
-  if (p) {
-    cudaStreamSynchronize(s);
-    cudaFree(p);
-  }
-  p = q;
-  cap = c;
-  return cudaSuccess;
-}
-
 double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// ---------------------------------------------------------------------------
-// Sampling orchestration.
-// ---------------------------------------------------------------------------
-// Runs one sampling launch and reads its counters back.
-gim_status run_pass(gim_ctx *ctx, int model, bool large, const WorkerScratch &ws, const SampleJob &job) {
-  SampleCtl init{};
-  init.store_tail = ctx->store_used;
-  CU(cudaMemcpyAsync(ctx->ctl, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
-  const uint32_t workers = large ? (uint32_t)std::min<uint64_t>(ws.workers, job.count) : ws.workers;
-  WorkerScratch w = ws;
-  w.workers = std::max<uint32_t>(workers, 1);
-  const int grid = (int)((w.workers + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  CU(cudaEventRecord(ctx->ev[6], ctx->stream));
-  CU(launch_sample(model, ctx->g, ctx->st, w, job, ctx->ctl, large, grid, kBlock, ctx->stream));
-  CU(cudaEventRecord(ctx->ev[7], ctx->stream));
-  ctx->launches++;
-  CU(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(SampleCtl), cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  float ms = 0;
-  cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);
-  ctx->t_kernel_ms[large ? 1 : 0] += ms;
-  ctx->n_kernel[large ? 1 : 0] += 1;
-  return GIM_OK;
-}
-
-// After a pass: account stored members, grow the store if reservations ran past it.
-gim_status settle_store(gim_ctx *ctx) {
-  const SampleCtl &c = *ctx->ctl_host;
-  if (c.err & kErrDeferredFull) return set_err(ctx, GIM_ERR_OOM, "deferred-set list overflow");
-  ctx->Z += c.members;
-  if (c.store_tail > ctx->st.cap) {
-    const uint64_t old = ctx->st.cap;
-    const uint64_t want = std::max<uint64_t>(old * 2, c.store_tail * 2);
-    uint64_t cap = ctx->st.cap;
-    CU(grow_copy(ctx->st.members, cap, want, ctx->st.cap, ctx->stream));
-    ctx->st.cap = cap;
-    ctx->store_used = old;   // the last partial reservation leaves a hole below the old end
-  } else {
-    ctx->store_used = c.store_tail;
-  }
-  return GIM_OK;
-}
-
-gim_status ensure_large_scratch(gim_ctx *ctx) {
-  if (ctx->ws_large.workers) return GIM_OK;
-  const uint32_t n = ctx->g.n;
-  const uint64_t per = ((uint64_t)n + 31) / 32 * 4 + (uint64_t)n * 4;
-  const uint32_t want = (uint32_t)ctx->sm_count * 16;
-  CU(alloc_scratch(ctx->ws_large, n, cap_workers(per, want), n, true, true, ctx->stream));
-  return GIM_OK;
-}
-
-// Appends RR sets [R, R + count) under (model, seed). On failure rolls the
-// occurrence counts back so that the collection is as before.
+// Appends RR sets [R, R + count) of ctx under (model, seed).
 gim_status sample_range(gim_ctx *ctx, int model, uint64_t seed, uint64_t count) {
-  const uint64_t R0 = ctx->R, Z0 = ctx->Z, used0 = ctx->store_used;
-  gim_status st = GIM_OK;
-  auto rollback = [&]() {
-    launch_uncount(ctx->st, R0, count, ctx->stream);
-    ctx->launches++;
-    cudaStreamSynchronize(ctx->stream);
-    ctx->Z = Z0;
-    ctx->store_used = used0;
-  };
-  // capacities
-  {
-    uint64_t cap = ctx->rr_cap, cap2 = ctx->rr_cap;
-    CU(grow_copy(ctx->st.rr_start, cap, R0 + count, R0, ctx->stream));
-    CU(grow_copy(ctx->st.rr_len, cap2, R0 + count, R0, ctx->stream));
-    ctx->rr_cap = std::min(cap, cap2);
-  }
-  CU(cudaMemsetAsync(ctx->st.rr_start + R0, 0xFF, count * sizeof(uint64_t), ctx->stream));
-  if (!ctx->st.members) {
-    uint64_t cap = 0;
-    CU(grow_copy(ctx->st.members, cap, kInitialStore, 0, ctx->stream));
-    ctx->st.cap = cap;
-  }
-  {
-    uint64_t dcap = ctx->deferred_cap;
-    CU(grow_copy(ctx->deferred, dcap, 2 * count, 0, ctx->stream));
-    ctx->deferred_cap = dcap;
-  }
-  uint64_t *list_a = ctx->deferred, *list_b = ctx->deferred + count;
-
-  SampleJob job{};
-  job.key = PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
-  job.j_begin = R0;
-  job.count = count;
-  job.j_list = nullptr;
-  job.deferred = list_a;
-  job.deferred_cap = count;
-  const WorkerScratch &ws = model == GIM_IC ? ctx->ws_small : ctx->ws_lt;
-  if ((st = run_pass(ctx, model, false, ws, job)) != GIM_OK) return rollback(), st;
-  if ((st = settle_store(ctx)) != GIM_OK) return rollback(), st;
-  uint64_t pending = ctx->ctl_host->n_deferred;
-  int rounds = 0;
-  while (pending > 0) {
-    if (++rounds > 40) {
-      rollback();
-      return set_err(ctx, GIM_ERR_OOM, "large-set pass did not converge");
-    }
-    if ((st = ensure_large_scratch(ctx)) != GIM_OK) return rollback(), st;
-    SampleJob lj = job;
-    lj.j_list = list_a;
-    lj.count = pending;
-    lj.deferred = list_b;
-    lj.deferred_cap = count;
-    if ((st = run_pass(ctx, model, true, ctx->ws_large, lj)) != GIM_OK) return rollback(), st;
-    if ((st = settle_store(ctx)) != GIM_OK) return rollback(), st;
-    pending = ctx->ctl_host->n_deferred;
-    std::swap(list_a, list_b);
-  }
-  ctx->R = R0 + count;
-  return GIM_OK;
+  std::vector<SampleJobH> jobs{SampleJobH{ctx, model, seed, count}};
+  return sample_jobs(jobs, ctx->stream);
 }
 
 gim_status check_ctx(gim_ctx *ctx) {
@@ -302,7 +113,7 @@ gim_status gim_create(gim_ctx **out, int device, void *stream) {
   if (!out) return GIM_ERR_ARG;
   *out = nullptr;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev || device >= kMaxDevices) {
     cudaGetLastError();
     return GIM_ERR_ARG;
   }
@@ -324,8 +135,11 @@ gim_status gim_create(gim_ctx **out, int device, void *stream) {
   }
   for (auto &e : ctx->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(GIM_ERR_CUDA);
-  if (cudaMalloc(&ctx->ctl, sizeof(SampleCtl)) != cudaSuccess) return fail(GIM_ERR_OOM);
-  if (cudaMallocHost(&ctx->ctl_host, sizeof(SampleCtl)) != cudaSuccess) return fail(GIM_ERR_OOM);
+  {
+    const gim_status st = shared_acquire(ctx);
+    if (st != GIM_OK) return fail(st);
+    ctx->shared_held = true;
+  }
   *out = ctx;
   return GIM_OK;
 }
@@ -339,13 +153,8 @@ void gim_destroy(gim_ctx *ctx) {
   dfree(ctx->st.rr_start);
   dfree(ctx->st.rr_len);
   dfree(ctx->st.cnt);
-  free_scratch(ctx->ws_small);
-  free_scratch(ctx->ws_lt);
-  free_scratch(ctx->ws_large);
-  dfree(ctx->deferred);
   free_select(ctx->sel);
-  dfree(ctx->ctl);
-  if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->shared_held) shared_release(ctx->device);
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -413,29 +222,18 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
                    (flags & kGraphBadWeight) ? "weight outside [0, 1]; " : "");
   }
 
-  // commit: replace the graph, empty the collection, size the scratch for n
+  // commit: replace the graph and empty the collection
   cudaStreamSynchronize(s);
   free_graph(ctx->g);
   ctx->g = g;
   ctx->has_graph = true;
   ctx->lt_ok = (flags & kGraphNotLT) ? 0 : 1;
   dfree(ctx->st.cnt);
-  free_scratch(ctx->ws_small);
-  free_scratch(ctx->ws_lt);
-  free_scratch(ctx->ws_large);
   free_select(ctx->sel);
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
   CU(cudaMalloc(&ctx->st.cnt, (uint64_t)n * 4 + 16));
   CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)n * 4 + 16, s));
-  {
-    const uint64_t per = ((uint64_t)n + 31) / 32 * 4 + kIcQueueCap * 4;
-    const uint32_t want = (uint32_t)ctx->sm_count * 64;   // up to 64 warps per SM
-    CU(alloc_scratch(ctx->ws_small, n, cap_workers(per, want), kIcQueueCap, true, true, s));
-    ctx->ws_lt = WorkerScratch{};
-    ctx->ws_lt.workers = (uint32_t)ctx->sm_count * 48;   // 6 blocks of 8 warps with 32 KB shared memory each
-    ctx->ws_lt.qcap = kLtPathCap;
-  }
   CU(cudaStreamSynchronize(s));
   return GIM_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -27,14 +28,15 @@ __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
   uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t a_lo = 0xD2511F53u * c0, a_hi = __umulhi(0xD2511F53u, c0);
-    const uint32_t b_lo = 0xCD9E8D57u * c2, b_hi = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t y0 = b_hi ^ c1 ^ k0;
-    const uint32_t y2 = a_hi ^ c3 ^ k1;
+    // one 32x32 -> 64-bit product per multiplier gives both halves
+    const unsigned long long a = (unsigned long long)0xD2511F53u * c0;
+    const unsigned long long b = (unsigned long long)0xCD9E8D57u * c2;
+    const uint32_t y0 = (uint32_t)(b >> 32) ^ c1 ^ k0;
+    const uint32_t y2 = (uint32_t)(a >> 32) ^ c3 ^ k1;
     c0 = y0;
-    c1 = b_lo;
+    c1 = (uint32_t)b;
     c2 = y2;
-    c3 = a_lo;
+    c3 = (uint32_t)a;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
@@ -74,41 +76,87 @@ struct DevStore {
   uint32_t *cnt = nullptr;       // n occurrence counts (Occur)
 };
 
+// One instance of a sampling launch: a graph, an RR collection and the ids
+// to draw. The kernels read these from a device array, so one launch can
+// serve many IMM instances (a single-instance call is a batch of one).
+struct InstDesc {
+  // graph
+  uint32_t n;
+  uint32_t pad0;
+  const uint32_t *off, *src, *thr, *rthr;
+  const uint64_t *cum;
+  // RR collection
+  uint32_t *members;
+  unsigned long long store_cap;
+  uint64_t *rr_start;
+  uint32_t *rr_len;
+  uint32_t *cnt;
+  // job: global items [item_begin, item_begin + count) are rr_ids j_begin ...
+  PhiloxKey key;
+  unsigned long long j_begin;
+  unsigned long long item_begin;
+  // written by the kernels
+  unsigned long long store_tail;     // store entries reserved (starts at the entries already used)
+  unsigned long long members_added;  // members of the sets stored by this launch
+};
+
 // Device counters of one sampling launch.
 struct SampleCtl {
   unsigned long long next;        // next work item
-  unsigned long long store_tail;  // store entries reserved
-  unsigned long long members;     // store entries of stored sets
-  unsigned long long n_deferred;  // sets handed to the large-set pass
+  unsigned long long n_deferred;  // sets handed to the next pass
   unsigned int err;               // error bits (kErr*)
   unsigned int pad;
 };
 
 enum : unsigned int { kErrDeferredFull = 1u };
 
-// Per-worker scratch for the sampling kernels.
-struct WorkerScratch {
-  uint32_t *bitmap = nullptr;    // words_per_worker per worker, all zero between sets
-  uint32_t *queue = nullptr;     // qcap per worker
-  uint64_t words_per_worker = 0;
-  uint32_t qcap = 0;
+// A sampling launch: the instances, the work items and where to defer.
+struct SampleLaunch {
+  InstDesc *inst;
+  uint32_t n_inst;
+  unsigned long long total_items;
+  const unsigned long long *items;   // nullable: item i is (instance << 32 | rr_id) = items[i]
+  unsigned long long *deferred;      // deferred sets, packed like items
+  unsigned long long deferred_cap;
+  SampleCtl *ctl;
+  uint32_t group_budget;             // common pass: edge groups (4 in-edges) a set may scan
+};
+
+constexpr uint32_t kQueueCap = 4096;        // common pass: members per set before it is deferred
+constexpr uint32_t kHashBits = 13;
+constexpr uint32_t kHashSlots = 1u << kHashBits;   // common pass: visited hash slots per worker
+constexpr uint32_t kLtPathCap = 1024;       // LT common pass: path length kept in shared memory
+
+// Scratch of the common (warp per set) IC pass; independent of n.
+struct CommonScratch {
+  uint32_t *queue = nullptr;              // kQueueCap per worker
+  unsigned long long *hash = nullptr;     // kHashSlots per worker: epoch << 32 | vertex
+  uint32_t *epoch = nullptr;              // per worker
   uint32_t workers = 0;
 };
 
-struct SampleJob {
-  PhiloxKey key;
-  uint64_t j_begin;              // first rr_id when items are a contiguous range
-  uint64_t count;                // number of work items
-  const uint64_t *j_list;        // nullable: item i is rr_id j_list[i]
-  uint64_t *deferred;            // where too-large (or unstorable) sets are listed
-  uint64_t deferred_cap;
+// Scratch of the large-set passes: per slot an n-bit visited bitmap (all zero
+// between sets) and an n-entry queue. IC uses one 512-thread block per slot,
+// LT one warp per slot.
+struct BigScratch {
+  uint32_t *bitmap = nullptr;
+  uint32_t *queue = nullptr;
+  uint64_t words_per_slot = 0;
+  uint32_t n_cap = 0;
+  uint32_t slots = 0;
 };
 
+constexpr int kBigBlock = 512;
+
 // Host launchers (sample.cu).
-cudaError_t launch_sample(int model, const DevGraph &g, const DevStore &st, const WorkerScratch &ws, const SampleJob &job,
-                          SampleCtl *ctl, bool large, int grid, int block, cudaStream_t s);
-cudaError_t launch_uncount(const DevStore &st, uint64_t j_begin, uint64_t count, cudaStream_t s);
+cudaError_t launch_ic_common(const SampleLaunch &L, const CommonScratch &cs, cudaStream_t s);
+cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s);
+cudaError_t launch_lt_common(const SampleLaunch &L, uint32_t grid, cudaStream_t s);
+cudaError_t launch_lt_large(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s);
+cudaError_t launch_uncount(const SampleLaunch &L, cudaStream_t s);
 cudaError_t launch_philox_rate(int blocks, uint32_t per_thread, uint32_t *sink, cudaStream_t s);
+int ic_common_blocks_per_sm();
+int lt_common_blocks_per_sm();
 
 // Graph preprocessing (graph.cu).
 cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_flags, cudaStream_t s);
@@ -131,6 +179,45 @@ struct SelectBuffers {
 
 cudaError_t run_select(const DevGraph &g, const DevStore &st, uint64_t R, uint64_t Z, uint32_t k, SelectBuffers &b,
                        int sm_count, cudaStream_t s, uint64_t *launches);
+
+// Per-device state shared by every context of the device: sampling scratch
+// and launch tables. Its mutex serialises the sampling of all contexts that
+// use the device.
+constexpr int kMaxDevices = 64;
+struct DeviceShared {
+  std::mutex mu;
+  int refs = 0;
+  int sm_count = 0;
+  uint32_t lt_grid = 0;
+  CommonScratch cs;
+  BigScratch big;
+  InstDesc *d_desc = nullptr;
+  uint64_t desc_cap = 0;
+  InstDesc *h_desc = nullptr;          // pinned
+  uint64_t h_desc_cap = 0;
+  unsigned long long *d_def = nullptr; // two deferred-set lists
+  uint64_t def_cap = 0;
+  SampleCtl *d_ctl = nullptr;
+  SampleCtl *h_ctl = nullptr;          // pinned
+};
+
+// A sampling job: RR sets [ctx->R, ctx->R + count) of ctx under (model, seed).
+struct SampleJobH {
+  gim_ctx *ctx;
+  int model;
+  uint64_t seed;
+  uint64_t count;
+};
+
+// engine.cu
+gim_status set_err(gim_ctx *ctx, gim_status st, const char *fmt, ...);
+gim_status cuda_err(gim_ctx *ctx, cudaError_t e, const char *what);
+gim_status shared_acquire(gim_ctx *ctx);
+void shared_release(int device);
+DeviceShared &device_shared(int device);
+gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s);
+template <typename T>
+cudaError_t grow_copy(T *&p, uint64_t &cap, uint64_t need, uint64_t keep, cudaStream_t s);
 
 }  // namespace gim
 
@@ -156,13 +243,7 @@ struct gim_ctx {
   uint64_t rr_cap = 0;
   gim::DevStore st;
 
-  // sampling scratch
-  gim::WorkerScratch ws_small, ws_lt, ws_large;   // IC common case, LT common case, large-set pass
-  gim::SampleCtl *ctl = nullptr;      // device
-  gim::SampleCtl *ctl_host = nullptr; // pinned mirror
-  uint64_t *deferred = nullptr;
-  uint64_t deferred_cap = 0;
-  int small_grid = 0, small_block = 0;
+  bool shared_held = false;       // holds a reference on the device's shared scratch
 
   gim::SelectBuffers sel;
 

@@ -1,29 +1,40 @@
 // RR-set sampling kernels (Sec. III-B to III-G; Alg. 3 and Alg. 6).
 //
-// A persistent grid of warps; each warp is one worker that takes RR-set ids
-// from a device work counter (the role of Alg. 6's N_RR) and builds one RR
-// set at a time:
-//   IC: reverse BFS over in-edges. Frontier vertices are taken in batches of
-//       up to 32, whose queue entries, offsets and row thresholds are loaded
-//       in one round trip; the rows are then scanned one after another by the
-//       whole warp, two groups of four consecutive edges per lane per step
-//       (one Philox call gives a group's four coin words). When all in-edges
-//       of a row share one probability (weighted cascade, uniform p) the
-//       row's threshold is used and the scan reads no edge data; otherwise
-//       one 16-byte load fetches the group's four thresholds. Live edges are
-//       buffered in shared memory; the buffer is resolved 32 edges at a time
-//       (read the source, test-and-set its bit in the worker's visited bitmap,
-//       append the newly visited to the worker's queue, which doubles as the
-//       member list: Sec. III-A, each vertex is expanded once).
-//   LT: the reverse walk of Sec. III-G: one draw per step, the chosen in-edge
-//       found by a 33-way warp search over the row's sorted cumulative
-//       thresholds, stop at no edge or at a vertex already on the path.
-// A finished set reserves its place in the store with one atomic (Alg. 6's
-// tail_RR) and is copied there; the occurrence counts (Occur) are bumped.
-// Sets that outgrow the worker's queue, or find the store full, are listed
-// as deferred and redone by the large-set pass (queue of n entries) after
-// the host has grown the store. RR set j depends only on (seed, j), so the
-// redo yields the same set.
+// Every launch serves a table of instances (graph + RR collection + ids to
+// draw); a device work counter hands out global items, and item i belongs to
+// the instance whose item range contains it (or names its instance
+// explicitly in the large-set passes). RR set j depends only on
+// (graph, seed, j), so which worker draws it, in which pass and in which
+// order never changes the set.
+//
+// IC, common pass: a persistent grid of warps, one RR set per warp at a time
+//   (the role of Alg. 6's N_RR counter is the work counter). Reverse BFS over
+//   in-edges: frontier vertices are taken in batches of up to 32 (queue
+//   entries, offsets and row thresholds fetched in one round trip); each row
+//   is scanned by the whole warp, two groups of four consecutive in-edges per
+//   lane per step, one Philox call giving a group's four coin words. A row
+//   whose in-edges share one probability (weighted cascade, uniform p) uses
+//   its common threshold, so the scan reads no edge data; otherwise one
+//   16-byte load fetches a group's four thresholds. Live edges are buffered
+//   in shared memory and resolved 32 per round trip: read the source,
+//   insert it into the worker's visited hash set, append the newly visited
+//   to the worker's queue (which doubles as the member list: Sec. III-A,
+//   each vertex is expanded once). The hash set is stamped with a per-set
+//   epoch, so it is never cleared. A set that outgrows the queue or scans
+//   more than its edge budget is abandoned and deferred.
+// IC, large-set pass: one 512-thread block per deferred set, with an n-bit
+//   visited bitmap and an n-entry queue. Each batch of up to 64 frontier
+//   vertices is cut into chunks of at most 2048 in-edges that the block's
+//   warps take from a shared counter, so the heavy tail of huge RR sets is
+//   spread over 16 warps. Only __syncthreads barriers are used.
+// LT: the reverse walk of Sec. III-G, one warp per walk: one draw per step,
+//   the chosen in-edge found by a 33-way warp search over the row's sorted
+//   cumulative thresholds, stop at no edge or at a vertex already on the
+//   path (common pass: path in shared memory; large pass: queue + bitmap).
+// A finished set reserves its place in its instance's store with one atomic
+// (Alg. 6's tail_RR) and is copied there; the occurrence counts (Occur) are
+// bumped. A set that finds its store full is deferred too; the host grows the
+// store and runs the large-set pass on the deferred list.
 #include "gim_internal.cuh"
 
 namespace gim {
@@ -32,61 +43,94 @@ namespace {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-__device__ __forceinline__ uint32_t comp(const uint4 &v, int q) {
-  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+// Instance of global item `item`: the last one whose item_begin <= item.
+__device__ __forceinline__ uint32_t find_inst(const InstDesc *inst, uint32_t n_inst, unsigned long long item) {
+  uint32_t lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (inst[mid].item_begin <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
 }
 
-__device__ __forceinline__ void defer(const SampleJob &job, SampleCtl *ctl, uint64_t j) {
-  const unsigned long long d = atomicAdd(&ctl->n_deferred, 1ull);
-  if (d < job.deferred_cap)
-    job.deferred[d] = j;
+// Decodes work item `item` of launch L into (instance, rr_id).
+__device__ __forceinline__ void decode_item(const SampleLaunch &L, unsigned long long item, uint32_t &ii, uint64_t &j) {
+  if (L.items) {
+    const unsigned long long p = L.items[item];
+    ii = (uint32_t)(p >> 32);
+    j = (uint32_t)p;
+  } else {
+    ii = find_inst(L.inst, L.n_inst, item);
+    j = L.inst[ii].j_begin + (item - L.inst[ii].item_begin);
+  }
+}
+
+__device__ __forceinline__ void defer(const SampleLaunch &L, uint32_t ii, uint64_t j) {
+  const unsigned long long d = atomicAdd(&L.ctl->n_deferred, 1ull);
+  if (d < L.deferred_cap)
+    L.deferred[d] = ((unsigned long long)ii << 32) | (uint32_t)j;
   else
-    atomicOr(&ctl->err, kErrDeferredFull);
+    atomicOr(&L.ctl->err, kErrDeferredFull);
 }
 
-// Copies the finished set q[0..size) to the store, bumps the occurrence
-// counts and clears the visited bits (bm may be null). Lane-uniform control.
-__device__ __forceinline__ void commit_set(const DevStore &st, const SampleJob &job, SampleCtl *ctl, uint64_t j,
-                                           const uint32_t *q, uint32_t size, uint32_t *bm) {
+// Warp-wide: copies the finished set q[0..size) to instance ii's store and
+// bumps its occurrence counts; clears the set's bitmap bits when bm != null.
+// Defers the set if the store is full.
+__device__ __forceinline__ void commit_warp(const SampleLaunch &L, uint32_t ii, uint64_t j, const uint32_t *q,
+                                            uint32_t size, uint32_t *bm) {
+  InstDesc &D = L.inst[ii];
   const uint32_t lane = lane_id();
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(&ctl->store_tail, (unsigned long long)size);
+  if (lane == 0) base = atomicAdd(&D.store_tail, (unsigned long long)size);
   base = __shfl_sync(kFullMask, base, 0);
-  const bool fits = base + size <= st.cap;
+  const bool fits = base + size <= D.store_cap;
+  uint32_t *members = D.members;
+  uint32_t *cnt = D.cnt;
   for (uint32_t i = lane; i < size; i += 32) {
     const uint32_t x = q[i];
     if (fits) {
-      st.members[base + i] = x;
-      atomicAdd(&st.cnt[x], 1u);
+      members[base + i] = x;
+      atomicAdd(&cnt[x], 1u);
     }
     if (bm) bm[x >> 5] = 0u;   // every set bit of the bitmap belongs to this set
   }
   __syncwarp();
   if (lane == 0) {
     if (fits) {
-      st.rr_start[j] = base;
-      st.rr_len[j] = size;
-      atomicAdd(&ctl->members, (unsigned long long)size);
+      D.rr_start[j] = base;
+      D.rr_len[j] = size;
+      atomicAdd(&D.members_added, (unsigned long long)size);
     } else {
-      defer(job, ctl, j);
+      defer(L, ii, j);
     }
   }
 }
 
+// The coin test (word >> 8) < t for a threshold t in [1, 2^24] is
+// word <= t * 256 - 1; lim() gives that bound (t = 0 rows are never scanned).
+__device__ __forceinline__ uint32_t lim(uint32_t t) { return (t << 8) - 1u; }
+
 // Coins of group grp (in-edges 4grp .. 4grp+3) for the row [s, e): bit qi is
 // set iff edge 4grp+qi lies in the row and is live. One Philox call yields
 // the four coin words. The threshold is the row's common one when it has
-// one (rt != kPerEdge), so the scan of such a row touches no memory.
+// one (rt != kPerEdge; rl = lim(rt)), so the scan of such a row touches no
+// memory.
 __device__ __forceinline__ uint32_t group_live(const uint32_t *__restrict__ thr, uint32_t grp, uint32_t s, uint32_t e,
-                                               uint32_t rt, uint32_t jlo, uint32_t jhi, PhiloxKey key) {
+                                               uint32_t rt, uint32_t rl, uint32_t jlo, uint32_t jhi, PhiloxKey key) {
   const uint4 r = philox10(grp, kTagEdge, jlo, jhi, key);
-  uint4 tv;
-  if (rt != kPerEdge)
-    tv = make_uint4(rt, rt, rt, rt);
-  else
-    tv = reinterpret_cast<const uint4 *>(thr)[grp];
-  uint32_t live = ((r.x >> 8) < tv.x ? 1u : 0u) | ((r.y >> 8) < tv.y ? 2u : 0u) | ((r.z >> 8) < tv.z ? 4u : 0u) |
-                  ((r.w >> 8) < tv.w ? 8u : 0u);
+  uint32_t live;
+  if (rt != kPerEdge) {
+    live = (r.x <= rl ? 1u : 0u) | (r.y <= rl ? 2u : 0u) | (r.z <= rl ? 4u : 0u) | (r.w <= rl ? 8u : 0u);
+  } else {
+    const uint4 tv = reinterpret_cast<const uint4 *>(thr)[grp];
+    // a zero threshold never fires; lim(0) wraps, so such edges are masked out
+    const uint32_t nz = (tv.x ? 1u : 0u) | (tv.y ? 2u : 0u) | (tv.z ? 4u : 0u) | (tv.w ? 8u : 0u);
+    live = ((r.x <= lim(tv.x) ? 1u : 0u) | (r.y <= lim(tv.y) ? 2u : 0u) | (r.z <= lim(tv.z) ? 4u : 0u) |
+            (r.w <= lim(tv.w) ? 8u : 0u)) & nz;
+  }
   const uint32_t e0 = grp << 2;            // s - 3 <= e0 <= e - 1
   if (e0 < s || e0 + 4 > e) {
     const uint32_t lo = s > e0 ? s - e0 : 0u;
@@ -96,13 +140,184 @@ __device__ __forceinline__ uint32_t group_live(const uint32_t *__restrict__ thr,
   return live;
 }
 
+// Exclusive prefix of a per-lane count across the warp; total = the sum.
+__device__ __forceinline__ uint32_t warp_excl(uint32_t mine, uint32_t &total) {
+  const uint32_t lane = lane_id();
+  uint32_t incl = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(kFullMask, incl, d);
+    if (lane >= (uint32_t)d) incl += o;
+  }
+  total = __shfl_sync(kFullMask, incl, 31);
+  return incl - mine;
+}
+
+// Appends the live edges of one warp step (the lane's groups ga and gb with
+// live masks la and lb) to cand, starting at pos.
+__device__ __forceinline__ void push_live(uint32_t *cand, uint32_t pos, uint32_t ga, uint32_t la, uint32_t gb,
+                                          uint32_t lb) {
+#pragma unroll
+  for (int qi = 0; qi < 4; ++qi)
+    if ((la >> qi) & 1u) cand[pos++] = (ga << 2) + qi;
+#pragma unroll
+  for (int qi = 0; qi < 4; ++qi)
+    if ((lb >> qi) & 1u) cand[pos++] = (gb << 2) + qi;
+}
+
 constexpr uint32_t kCandCap = 512;   // per-warp buffer of live edges awaiting their visited test
 
-// Resolves the buffered live edges cand[0..ncand): reads each one's source,
-// test-and-sets its visited bit and appends the newly visited sources to the
-// queue (32 edges per round trip). Lane-uniform control.
-__device__ __forceinline__ void ic_flush(const uint32_t *__restrict__ src, const uint32_t *cand, uint32_t ncand,
-                                         uint32_t *bm, uint32_t *q, uint32_t qcap, uint32_t &tail, bool &overflow) {
+// Visited set of the common pass: open addressing over kHashSlots 64-bit
+// slots holding epoch << 32 | vertex; a slot whose epoch is not the current
+// set's is free. Returns true iff u was not in the set and is now.
+__device__ __forceinline__ bool hash_insert(unsigned long long *ht, uint32_t epoch, uint32_t u) {
+  const unsigned long long want = ((unsigned long long)epoch << 32) | u;
+  uint32_t h = (u * 0x9E3779B1u) >> (32 - kHashBits);
+  for (uint32_t probe = 0; probe < kHashSlots; ++probe) {
+    unsigned long long cur = ht[h];
+    for (int tries = 0; tries < 64; ++tries) {       // a slot changes at most once per set
+      if ((uint32_t)(cur >> 32) == epoch) {
+        if ((uint32_t)cur == u) return false;
+        break;
+      }
+      const unsigned long long prev = atomicCAS(&ht[h], cur, want);
+      if (prev == cur) return true;
+      cur = prev;
+    }
+    h = (h + 1) & (kHashSlots - 1);
+  }
+  return false;   // unreachable: at most kQueueCap + kCandCap < kHashSlots vertices per set
+}
+
+// Resolves the buffered live edges cand[0..ncand) of the common pass.
+__device__ __forceinline__ void common_flush(const uint32_t *__restrict__ src, const uint32_t *cand, uint32_t ncand,
+                                             unsigned long long *ht, uint32_t epoch, uint32_t *q, uint32_t &tail,
+                                             bool &overflow) {
+  const uint32_t lane = lane_id();
+  const uint32_t below = (1u << lane) - 1u;
+  __syncwarp();
+  for (uint32_t i0 = 0; i0 < ncand; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    uint32_t u = 0;
+    bool fresh = false;
+    if (i < ncand) {
+      u = src[cand[i]];
+      fresh = hash_insert(ht, epoch, u);
+    }
+    const uint32_t fm = __ballot_sync(kFullMask, fresh);
+    if (fm) {
+      const uint32_t pos = tail + __popc(fm & below);
+      if (fresh && pos < kQueueCap) q[pos] = u;
+      tail += __popc(fm);
+      if (tail > kQueueCap) {
+        tail = kQueueCap;
+        overflow = true;   // the set is abandoned; its hash entries expire with the epoch
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, CommonScratch cs) {
+  __shared__ uint32_t cand_all[8][kCandCap];
+  const uint32_t lane = lane_id();
+  const uint32_t worker = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (worker >= cs.workers) return;
+  uint32_t *cand = cand_all[threadIdx.x >> 5];
+  uint32_t *q = cs.queue + (uint64_t)worker * kQueueCap;
+  unsigned long long *ht = cs.hash + (uint64_t)worker * kHashSlots;
+  uint32_t epoch = cs.epoch[worker];
+
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&L.ctl->next, 1ull);
+    item = __shfl_sync(kFullMask, item, 0);
+    if (item >= L.total_items) break;
+    uint32_t ii = 0;
+    uint64_t j = 0;
+    if (lane == 0) decode_item(L, item, ii, j);
+    ii = __shfl_sync(kFullMask, ii, 0);
+    j = __shfl_sync(kFullMask, j, 0);
+    const InstDesc &D = L.inst[ii];
+    const uint32_t *__restrict__ off = D.off;
+    const uint32_t *__restrict__ rthr = D.rthr;
+    const uint32_t *__restrict__ thr = D.thr;
+    const uint32_t *__restrict__ src = D.src;
+    const PhiloxKey key = D.key;
+    const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
+
+    if (++epoch == 0xFFFFFFFFu) {              // epochs ran out: wipe the table once
+      for (uint32_t h = lane; h < kHashSlots; h += 32) ht[h] = 0ull;
+      __syncwarp();
+      epoch = 1;
+    }
+    const uint32_t root = draw_root(key, j, D.n);
+    if (lane == 0) {
+      q[0] = root;
+      ht[(root * 0x9E3779B1u) >> (32 - kHashBits)] = ((unsigned long long)epoch << 32) | root;
+    }
+    uint32_t head = 0, tail = 1, scanned = 0;
+    bool overflow = false;
+    while (head < tail && !overflow) {
+      __syncwarp();
+      if (scanned > L.group_budget) {          // a heavy set: hand it to the large-set pass
+        overflow = true;
+        break;
+      }
+      const uint32_t nb = tail - head < 32u ? tail - head : 32u;
+      uint32_t rs = 0, re = 0, rr = 0;
+      if (lane < nb) {
+        const uint32_t v = q[head + lane];
+        rs = off[v];
+        re = off[v + 1];
+        rr = rthr[v];
+      }
+      head += nb;
+      uint32_t ncand = 0;
+      for (uint32_t b = 0; b < nb && !overflow; ++b) {
+        const uint32_t s = __shfl_sync(kFullMask, rs, b), e = __shfl_sync(kFullMask, re, b);
+        const uint32_t rt = __shfl_sync(kFullMask, rr, b);
+        if (e <= s || rt == 0u) continue;      // a row whose coins are all 0 adds nothing
+        const uint32_t rl = lim(rt);
+        const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
+        scanned += g1 - g0 + 1;
+        for (uint32_t base = g0; base <= g1 && !overflow; base += 64) {   // 64 groups per warp step
+          const uint32_t ga = base + lane, gb = base + 32 + lane;
+          uint32_t la = 0, lb = 0;
+          if (ga <= g1) la = group_live(thr, ga, s, e, rt, rl, jlo, jhi, key);
+          if (gb <= g1) lb = group_live(thr, gb, s, e, rt, rl, jlo, jhi, key);
+          if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
+          uint32_t total;
+          const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
+          if (ncand + total > kCandCap) {
+            common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
+            ncand = 0;
+          }
+          push_live(cand, ncand + excl, ga, la, gb, lb);
+          ncand += total;
+        }
+      }
+      common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
+    }
+    if (overflow) {
+      if (lane == 0) defer(L, ii, j);
+      continue;
+    }
+    commit_warp(L, ii, j, q, tail, nullptr);
+  }
+  if (lane == 0) cs.epoch[worker] = epoch;
+}
+
+// ---------------------------------------------------------------------------
+// IC large-set pass: one block of kBigBlock threads per RR set.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kBatch = 256;             // frontier vertices per block step
+constexpr uint32_t kChunkGroups = 256;       // groups (1024 in-edges) per chunk
+constexpr uint32_t kBigWarps = kBigBlock / 32;
+constexpr uint32_t kBigCand = 256;           // per-warp candidate buffer
+
+__device__ __forceinline__ void block_flush(const uint32_t *__restrict__ src, const uint32_t *cand, uint32_t ncand,
+                                            uint32_t *bm, uint32_t *q, uint32_t *s_tail) {
   const uint32_t lane = lane_id();
   const uint32_t below = (1u << lane) - 1u;
   __syncwarp();
@@ -117,106 +332,149 @@ __device__ __forceinline__ void ic_flush(const uint32_t *__restrict__ src, const
     }
     const uint32_t fm = __ballot_sync(kFullMask, fresh);
     if (fm) {
-      const uint32_t pos = tail + __popc(fm & below);
-      if (fresh) {
-        if (pos < qcap)
-          q[pos] = u;
-        else
-          atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));   // not queued: leave no trace
-      }
-      tail += __popc(fm);
-      if (tail > qcap) {
-        tail = qcap;
-        overflow = true;
-      }
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(s_tail, (uint32_t)__popc(fm));
+      base = __shfl_sync(kFullMask, base, 0);
+      if (fresh) q[base + __popc(fm & below)] = u;   // a vertex enters once: the queue holds n
     }
   }
   __syncwarp();
 }
 
-template <bool kLarge>
-__global__ void __launch_bounds__(256) sample_ic_kernel(DevGraph g, DevStore st, WorkerScratch ws, SampleJob job,
-                                                        SampleCtl *ctl) {
-  __shared__ uint32_t cand_all[8][kCandCap];
-  const uint32_t lane = lane_id();
-  const uint32_t worker = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (worker >= ws.workers) return;
-  uint32_t *cand = cand_all[threadIdx.x >> 5];
-  uint32_t *bm = ws.bitmap + (uint64_t)worker * ws.words_per_worker;
-  uint32_t *q = ws.queue + (uint64_t)worker * ws.qcap;
-  const uint32_t qcap = ws.qcap;
+__global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, BigScratch bs) {
+  __shared__ uint32_t cand_all[kBigWarps][kBigCand];
+  __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
+  __shared__ uint32_t w_tot[kBigWarps];
+  __shared__ unsigned long long s_item, s_base;
+  __shared__ uint32_t s_head, s_tail, s_next;
+  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  uint32_t *cand = cand_all[warp];
+  uint32_t *bm = bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot;
+  uint32_t *q = bs.queue + (uint64_t)blockIdx.x * bs.n_cap;
 
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&ctl->next, 1ull);
-    item = __shfl_sync(kFullMask, item, 0);
-    if (item >= job.count) break;
-    const uint64_t j = job.j_list ? job.j_list[item] : job.j_begin + item;
+    if (tid == 0) s_item = atomicAdd(&L.ctl->next, 1ull);
+    __syncthreads();
+    const unsigned long long item = s_item;
+    if (item >= L.total_items) break;
+    uint32_t ii;
+    uint64_t j;
+    decode_item(L, item, ii, j);
+    const InstDesc &D = L.inst[ii];
+    const uint32_t *__restrict__ off = D.off;
+    const uint32_t *__restrict__ rthr = D.rthr;
+    const uint32_t *__restrict__ thr = D.thr;
+    const uint32_t *__restrict__ src = D.src;
+    const PhiloxKey key = D.key;
     const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
-    const uint32_t root = draw_root(job.key, j, g.n);
-    if (lane == 0) {
+    if (tid == 0) {
+      const uint32_t root = draw_root(key, j, D.n);
       q[0] = root;
-      bm[root >> 5] = 1u << (root & 31u);   // the worker's bitmap is all zero here
+      bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
+      s_head = 0;
+      s_tail = 1;
     }
-    uint32_t head = 0, tail = 1;
-    bool overflow = false;
-    while (head < tail && !overflow) {
-      __syncwarp();
-      // a batch of up to 32 frontier vertices: their rows are fetched at once
-      const uint32_t nb = tail - head < 32u ? tail - head : 32u;
-      uint32_t rs = 0, re = 0, rr = 0;
-      if (lane < nb) {
-        const uint32_t v = q[head + lane];
-        rs = g.off[v];
-        re = g.off[v + 1];
-        rr = g.rthr[v];
+    __syncthreads();
+    uint32_t ncand = 0;                        // this warp's buffered live edges
+    for (;;) {
+      const uint32_t head = s_head, tail = s_tail;
+      if (head >= tail) break;
+      const uint32_t nb = tail - head < kBatch ? tail - head : kBatch;
+      uint32_t nch = 0;                        // chunks of this thread's frontier vertex
+      if (tid < nb) {
+        const uint32_t v = q[head + tid];
+        const uint32_t s = off[v], e = off[v + 1], rt = rthr[v];
+        b_s[tid] = s;
+        b_e[tid] = e;
+        b_rt[tid] = rt;
+        nch = (e > s && rt != 0u) ? (((e - 1) >> 2) - (s >> 2) + kChunkGroups) / kChunkGroups : 0u;
       }
-      head += nb;
-      uint32_t ncand = 0;
-      for (uint32_t b = 0; b < nb && !overflow; ++b) {
-        const uint32_t s = __shfl_sync(kFullMask, rs, b), e = __shfl_sync(kFullMask, re, b);
-        const uint32_t rt = __shfl_sync(kFullMask, rr, b);
-        if (e <= s || rt == 0u) continue;      // a row whose coins are all 0 adds nothing
+      // block-wide exclusive prefix of the chunk counts (threads >= kBatch hold 0)
+      uint32_t wsum;
+      const uint32_t wex = warp_excl(nch, wsum);
+      if (lane == 0) w_tot[warp] = wsum;
+      if (tid == 0) s_next = 0;
+      __syncthreads();
+      uint32_t before = 0;
+      for (uint32_t w = 0; w < warp; ++w) before += w_tot[w];
+      if (tid < nb) b_pre[tid] = before + wex;
+      if (tid == nb - 1) b_pre[nb] = before + wex + nch;
+      __syncthreads();
+      const uint32_t nchunks = b_pre[nb];
+      for (;;) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&s_next, 1u);
+        c = __shfl_sync(kFullMask, c, 0);
+        if (c >= nchunks) break;
+        uint32_t lo = 0, hi = nb - 1;          // vertex b with b_pre[b] <= c < b_pre[b + 1]
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (b_pre[mid] <= c)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const uint32_t s = b_s[lo], e = b_e[lo], rt = b_rt[lo], rl = lim(rt);
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
-        for (uint32_t base = g0; base <= g1; base += 64) {
+        const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkGroups;
+        const uint32_t c1 = c0 + kChunkGroups - 1 < g1 ? c0 + kChunkGroups - 1 : g1;
+        for (uint32_t base = c0; base <= c1; base += 64) {   // 64 groups per warp step
           const uint32_t ga = base + lane, gb = base + 32 + lane;
           uint32_t la = 0, lb = 0;
-          if (ga <= g1) la = group_live(g.thr, ga, s, e, rt, jlo, jhi, job.key);
-          if (gb <= g1) lb = group_live(g.thr, gb, s, e, rt, jlo, jhi, job.key);
-          const uint32_t mine = __popc(la) + __popc(lb);
-          if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
-          uint32_t incl = mine;
-#pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t o = __shfl_up_sync(kFullMask, incl, d);
-            if (lane >= (uint32_t)d) incl += o;
-          }
-          const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-          if (ncand + total > kCandCap) {
-            ic_flush(g.src, cand, ncand, bm, q, qcap, tail, overflow);
+          if (ga <= c1) la = group_live(thr, ga, s, e, rt, rl, jlo, jhi, key);
+          if (gb <= c1) lb = group_live(thr, gb, s, e, rt, rl, jlo, jhi, key);
+          if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
+          uint32_t total;
+          const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
+          if (ncand + total > kBigCand) {
+            block_flush(src, cand, ncand, bm, q, &s_tail);
             ncand = 0;
           }
-          uint32_t pos = ncand + incl - mine;
-#pragma unroll
-          for (int qi = 0; qi < 4; ++qi)
-            if ((la >> qi) & 1u) cand[pos++] = (ga << 2) + qi;
-#pragma unroll
-          for (int qi = 0; qi < 4; ++qi)
-            if ((lb >> qi) & 1u) cand[pos++] = (gb << 2) + qi;
+          push_live(cand, ncand + excl, ga, la, gb, lb);
           ncand += total;
         }
       }
-      ic_flush(g.src, cand, ncand, bm, q, qcap, tail, overflow);
+      // Resolve the buffered live edges only when the frontier runs low: while
+      // at least a batch of queued vertices is still unexpanded, the next
+      // batch does not need them, and the warps keep them buffered.
+      if (tail - (head + nb) < kBatch) {
+        block_flush(src, cand, ncand, bm, q, &s_tail);
+        ncand = 0;
+      }
+      __syncthreads();                         // appended vertices visible; batch done
+      if (tid == 0) s_head = head + nb;
+      __syncthreads();
     }
-    if (overflow) {
-      for (uint32_t i = lane; i < tail; i += 32) bm[q[i] >> 5] = 0u;
-      __syncwarp();
-      if (lane == 0) defer(job, ctl, j);
-      continue;
+    // commit the set: q[0 .. s_tail)
+    const uint32_t size = s_tail;
+    if (tid == 0) s_base = atomicAdd(&L.inst[ii].store_tail, (unsigned long long)size);
+    __syncthreads();
+    const unsigned long long base = s_base;
+    const bool fits = base + size <= D.store_cap;
+    for (uint32_t i = tid; i < size; i += kBigBlock) {
+      const uint32_t x = q[i];
+      if (fits) {
+        D.members[base + i] = x;
+        atomicAdd(&D.cnt[x], 1u);
+      }
+      bm[x >> 5] = 0u;
     }
-    commit_set(st, job, ctl, j, q, tail, bm);
+    if (tid == 0) {
+      if (fits) {
+        D.rr_start[j] = base;
+        D.rr_len[j] = size;
+        atomicAdd(&L.inst[ii].members_added, (unsigned long long)size);
+      } else {
+        defer(L, ii, j);
+      }
+    }
+    __syncthreads();
   }
 }
+
+// ---------------------------------------------------------------------------
+// LT walk.
+// ---------------------------------------------------------------------------
 
 // Finds the first index a in [s, e) with U < cum[a], or e if there is none.
 // cum is non-decreasing within the row. Warp-uniform result.
@@ -243,42 +501,48 @@ __device__ __forceinline__ uint32_t lt_pick(const uint64_t *__restrict__ cum, ui
   return b ? lo + (uint32_t)(__ffs(b) - 1) : hi;
 }
 
-// LT walk. kLarge = false keeps the path in shared memory (capacity qcap per
-// warp) and tests "already visited" by a warp-wide compare against the path;
-// kLarge = true keeps it in the worker's global queue with the visited bitmap.
+// kLarge = false keeps the path in shared memory (kLtPathCap per warp) and
+// tests "already visited" by a warp-wide compare against the path; kLarge =
+// true is one warp per block with the slot's bitmap and n-entry queue.
 template <bool kLarge>
-__global__ void __launch_bounds__(256) sample_lt_kernel(DevGraph g, DevStore st, WorkerScratch ws, SampleJob job,
-                                                        SampleCtl *ctl) {
+__global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, BigScratch bs) {
   extern __shared__ uint32_t smem[];
   const uint32_t lane = lane_id();
-  const uint32_t worker = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (worker >= ws.workers) return;
-  const uint32_t qcap = ws.qcap;
-  uint32_t *bm = kLarge ? ws.bitmap + (uint64_t)worker * ws.words_per_worker : nullptr;
-  uint32_t *path = kLarge ? ws.queue + (uint64_t)worker * qcap : smem + (threadIdx.x >> 5) * qcap;
+  const uint32_t cap = kLarge ? bs.n_cap : kLtPathCap;
+  uint32_t *bm = kLarge ? bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot : nullptr;
+  uint32_t *path = kLarge ? bs.queue + (uint64_t)blockIdx.x * bs.n_cap : smem + (threadIdx.x >> 5) * kLtPathCap;
 
   for (;;) {
     unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&ctl->next, 1ull);
+    if (lane == 0) item = atomicAdd(&L.ctl->next, 1ull);
     item = __shfl_sync(kFullMask, item, 0);
-    if (item >= job.count) break;
-    const uint64_t j = job.j_list ? job.j_list[item] : job.j_begin + item;
+    if (item >= L.total_items) break;
+    uint32_t ii = 0;
+    uint64_t j = 0;
+    if (lane == 0) decode_item(L, item, ii, j);
+    ii = __shfl_sync(kFullMask, ii, 0);
+    j = __shfl_sync(kFullMask, j, 0);
+    const InstDesc &D = L.inst[ii];
+    const uint32_t *__restrict__ off = D.off;
+    const uint64_t *__restrict__ cum = D.cum;
+    const uint32_t *__restrict__ src = D.src;
+    const PhiloxKey key = D.key;
     const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
-    uint32_t x = draw_root(job.key, j, g.n);
+    uint32_t x = draw_root(key, j, D.n);
     if (lane == 0) {
       path[0] = x;
       if (kLarge) bm[x >> 5] = 1u << (x & 31u);
     }
     __syncwarp();
-    uint32_t L = 1;
+    uint32_t len = 1;
     bool overflow = false;
     for (;;) {
-      const uint32_t U = philox10(x, kTagStep, jlo, jhi, job.key).x;
-      const uint32_t s = g.off[x], e = g.off[x + 1];
+      const uint32_t U = philox10(x, kTagStep, jlo, jhi, key).x;
+      const uint32_t s = off[x], e = off[x + 1];
       if (e == s) break;
-      const uint32_t a = lt_pick(g.cum, s, e, U);
+      const uint32_t a = lt_pick(cum, s, e, U);
       if (a >= e) break;
-      const uint32_t u = g.src[a];
+      const uint32_t u = src[a];
       bool seen;
       if (kLarge) {
         uint32_t old = 0;
@@ -286,45 +550,48 @@ __global__ void __launch_bounds__(256) sample_lt_kernel(DevGraph g, DevStore st,
         seen = (__shfl_sync(kFullMask, old, 0) >> (u & 31u)) & 1u;
       } else {
         bool hit = false;
-        for (uint32_t i = lane; i < L; i += 32) hit |= (path[i] == u);
+        for (uint32_t i = lane; i < len; i += 32) hit |= (path[i] == u);
         seen = __any_sync(kFullMask, hit);
       }
       if (seen) break;
-      if (L == qcap) {
+      if (len == cap) {
         overflow = true;
         if (kLarge && lane == 0) atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));
         break;
       }
-      if (lane == 0) path[L] = u;
-      ++L;
+      if (lane == 0) path[len] = u;
+      ++len;
       __syncwarp();
       x = u;
     }
     if (overflow) {
       if (kLarge) {
-        for (uint32_t i = lane; i < L; i += 32) bm[path[i] >> 5] = 0u;
+        for (uint32_t i = lane; i < len; i += 32) bm[path[i] >> 5] = 0u;
         __syncwarp();
       }
-      if (lane == 0) defer(job, ctl, j);
+      if (lane == 0) defer(L, ii, j);
       continue;
     }
-    commit_set(st, job, ctl, j, path, L, bm);
+    commit_warp(L, ii, j, path, len, bm);
     __syncwarp();
   }
 }
 
-// Rollback helper: lowers the occurrence counts of the sets among
-// [j_begin, j_begin + count) that were stored (rr_start != kNoStart).
-__global__ void uncount_kernel(DevStore st, uint64_t j_begin, uint64_t count) {
+// Rollback helper: lowers the occurrence counts of the sets of a launch's
+// items that were stored (rr_start != kNoStart).
+__global__ void uncount_kernel(SampleLaunch L) {
   const uint32_t lane = lane_id();
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t i = warp; i < count; i += nwarps) {
-    const uint64_t j = j_begin + i;
-    const uint64_t b = st.rr_start[j];
+  for (uint64_t item = warp; item < L.total_items; item += nwarps) {
+    uint32_t ii;
+    uint64_t j;
+    decode_item(L, item, ii, j);
+    const InstDesc &D = L.inst[ii];
+    const uint64_t b = D.rr_start[j];
     if (b == kNoStart) continue;
-    const uint32_t len = st.rr_len[j];
-    for (uint32_t t = lane; t < len; t += 32) atomicSub(&st.cnt[st.members[b + t]], 1u);
+    const uint32_t len = D.rr_len[j];
+    for (uint32_t t = lane; t < len; t += 32) atomicSub(&D.cnt[D.members[b + t]], 1u);
   }
 }
 
@@ -345,34 +612,49 @@ __global__ void __launch_bounds__(256) philox_rate_kernel(PhiloxKey key, uint32_
 
 }  // namespace
 
+int ic_common_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ic_common_kernel, 256, 0) != cudaSuccess) b = 4;
+  return b > 0 ? b : 1;
+}
+
+int lt_common_blocks_per_sm() {
+  int b = 0;
+  const size_t sm = 8 * kLtPathCap * sizeof(uint32_t);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lt_kernel<false>, 256, sm) != cudaSuccess) b = 4;
+  return b > 0 ? b : 1;
+}
+
+cudaError_t launch_ic_common(const SampleLaunch &L, const CommonScratch &cs, cudaStream_t s) {
+  ic_common_kernel<<<(cs.workers + 7) / 8, 256, 0, s>>>(L, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s) {
+  ic_block_kernel<<<grid, kBigBlock, 0, s>>>(L, bs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lt_common(const SampleLaunch &L, uint32_t grid, cudaStream_t s) {
+  lt_kernel<false><<<grid, 256, 8 * kLtPathCap * sizeof(uint32_t), s>>>(L, BigScratch{});
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lt_large(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s) {
+  lt_kernel<true><<<grid, 32, 0, s>>>(L, bs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_uncount(const SampleLaunch &L, cudaStream_t s) {
+  if (L.total_items == 0) return cudaSuccess;
+  uint64_t blocks = (L.total_items + 7) / 8;
+  if (blocks > 4096) blocks = 4096;
+  uncount_kernel<<<(unsigned)blocks, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_philox_rate(int blocks, uint32_t per_thread, uint32_t *sink, cudaStream_t s) {
   philox_rate_kernel<<<blocks, 256, 0, s>>>(PhiloxKey{0x01234567u, 0x89ABCDEFu}, per_thread, sink);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sample(int model, const DevGraph &g, const DevStore &st, const WorkerScratch &ws, const SampleJob &job,
-                          SampleCtl *ctl, bool large, int grid, int block, cudaStream_t s) {
-  if (model == GIM_IC) {
-    if (large)
-      sample_ic_kernel<true><<<grid, block, 0, s>>>(g, st, ws, job, ctl);
-    else
-      sample_ic_kernel<false><<<grid, block, 0, s>>>(g, st, ws, job, ctl);
-  } else {
-    if (large) {
-      sample_lt_kernel<true><<<grid, block, 0, s>>>(g, st, ws, job, ctl);
-    } else {
-      const size_t sm = (size_t)(block / 32) * ws.qcap * sizeof(uint32_t);
-      sample_lt_kernel<false><<<grid, block, sm, s>>>(g, st, ws, job, ctl);
-    }
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_uncount(const DevStore &st, uint64_t j_begin, uint64_t count, cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  uint64_t blocks = (count + 7) / 8;
-  if (blocks > 4096) blocks = 4096;
-  uncount_kernel<<<(unsigned)blocks, 256, 0, s>>>(st, j_begin, count);
   return cudaGetLastError();
 }
 
