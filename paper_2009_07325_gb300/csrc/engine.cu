@@ -240,8 +240,9 @@ gim_status run_one(gim_ctx *ctx, DeviceShared &D, int model, std::vector<SampleJ
   CU(cudaEventRecord(ctx->ev[6], s));
   cudaError_t e;
   if (model == GIM_IC) {
-    e = P.large ? launch_ic_block(L, D.big, (uint32_t)std::min<uint64_t>(P.items, D.big.slots), s)
-                : launch_ic_common(L, D.cs, s);
+    const InstDesc *one = ni == 1 ? &D.h_desc[0] : nullptr;
+    e = P.large ? launch_ic_block(L, D.big, (uint32_t)std::min<uint64_t>(P.items, D.big.slots), one, s)
+                : launch_ic_common(L, D.cs, one, s);
   } else {
     e = P.large ? launch_lt_large(L, D.big, (uint32_t)std::min<uint64_t>(P.items, D.big.slots), s)
                 : launch_lt_common(L, D.lt_grid, s);

@@ -149,8 +149,11 @@ struct BigScratch {
 constexpr int kBigBlock = 512;
 
 // Host launchers (sample.cu).
-cudaError_t launch_ic_common(const SampleLaunch &L, const CommonScratch &cs, cudaStream_t s);
-cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s);
+// `one` (nullable): the launch's only instance, passed by value so that the
+// kernel reads its fields from kernel parameters.
+cudaError_t launch_ic_common(const SampleLaunch &L, const CommonScratch &cs, const InstDesc *one, cudaStream_t s);
+cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, const InstDesc *one,
+                            cudaStream_t s);
 cudaError_t launch_lt_common(const SampleLaunch &L, uint32_t grid, cudaStream_t s);
 cudaError_t launch_lt_large(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s);
 cudaError_t launch_uncount(const SampleLaunch &L, cudaStream_t s);

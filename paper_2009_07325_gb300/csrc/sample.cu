@@ -68,6 +68,40 @@ __device__ __forceinline__ void decode_item(const SampleLaunch &L, unsigned long
   }
 }
 
+// The fields of an instance a kernel reads. Single-instance launches build it
+// from a kernel parameter, so every field is warp-uniform (uniform registers);
+// batched launches read the instance's row of the descriptor table.
+struct InstView {
+  uint32_t n;
+  const uint32_t *off, *src, *thr, *rthr;
+  const uint64_t *cum;
+  uint32_t *members;
+  unsigned long long store_cap;
+  uint64_t *rr_start;
+  uint32_t *rr_len;
+  uint32_t *cnt;
+  PhiloxKey key;
+  unsigned long long j_begin;
+};
+
+__device__ __forceinline__ InstView view_of(const InstDesc &d) {
+  return InstView{d.n, d.off, d.src, d.thr, d.rthr, d.cum, d.members, d.store_cap, d.rr_start, d.rr_len, d.cnt,
+                  d.key, d.j_begin};
+}
+
+// Instance and rr_id of work item `item`, and the instance's view.
+template <bool kOne>
+__device__ __forceinline__ InstView item_view(const SampleLaunch &L, const InstDesc &one, unsigned long long item,
+                                              uint32_t &ii, uint64_t &j) {
+  if (kOne) {
+    ii = 0;
+    j = L.items ? (uint64_t)(uint32_t)L.items[item] : one.j_begin + item;
+    return view_of(one);
+  }
+  decode_item(L, item, ii, j);
+  return view_of(L.inst[ii]);
+}
+
 __device__ __forceinline__ void defer(const SampleLaunch &L, uint32_t ii, uint64_t j) {
   const unsigned long long d = atomicAdd(&L.ctl->n_deferred, 1ull);
   if (d < L.deferred_cap)
@@ -79,16 +113,16 @@ __device__ __forceinline__ void defer(const SampleLaunch &L, uint32_t ii, uint64
 // Warp-wide: copies the finished set q[0..size) to instance ii's store and
 // bumps its occurrence counts; clears the set's bitmap bits when bm != null.
 // Defers the set if the store is full.
-__device__ __forceinline__ void commit_warp(const SampleLaunch &L, uint32_t ii, uint64_t j, const uint32_t *q,
-                                            uint32_t size, uint32_t *bm) {
+__device__ __forceinline__ void commit_warp(const SampleLaunch &L, const InstView &V, uint32_t ii, uint64_t j,
+                                            const uint32_t *q, uint32_t size, uint32_t *bm) {
   InstDesc &D = L.inst[ii];
   const uint32_t lane = lane_id();
   unsigned long long base = 0;
   if (lane == 0) base = atomicAdd(&D.store_tail, (unsigned long long)size);
   base = __shfl_sync(kFullMask, base, 0);
-  const bool fits = base + size <= D.store_cap;
-  uint32_t *members = D.members;
-  uint32_t *cnt = D.cnt;
+  const bool fits = base + size <= V.store_cap;
+  uint32_t *members = V.members;
+  uint32_t *cnt = V.cnt;
   for (uint32_t i = lane; i < size; i += 32) {
     const uint32_t x = q[i];
     if (fits) {
@@ -100,8 +134,8 @@ __device__ __forceinline__ void commit_warp(const SampleLaunch &L, uint32_t ii, 
   __syncwarp();
   if (lane == 0) {
     if (fits) {
-      D.rr_start[j] = base;
-      D.rr_len[j] = size;
+      V.rr_start[j] = base;
+      V.rr_len[j] = size;
       atomicAdd(&D.members_added, (unsigned long long)size);
     } else {
       defer(L, ii, j);
@@ -218,7 +252,8 @@ __device__ __forceinline__ void common_flush(const uint32_t *__restrict__ src, c
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, CommonScratch cs) {
+template <bool kOne>
+__global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, CommonScratch cs, InstDesc one) {
   __shared__ uint32_t cand_all[8][kCandCap];
   const uint32_t lane = lane_id();
   const uint32_t worker = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -235,15 +270,12 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
     if (item >= L.total_items) break;
     uint32_t ii = 0;
     uint64_t j = 0;
-    if (lane == 0) decode_item(L, item, ii, j);
-    ii = __shfl_sync(kFullMask, ii, 0);
-    j = __shfl_sync(kFullMask, j, 0);
-    const InstDesc &D = L.inst[ii];
-    const uint32_t *__restrict__ off = D.off;
-    const uint32_t *__restrict__ rthr = D.rthr;
-    const uint32_t *__restrict__ thr = D.thr;
-    const uint32_t *__restrict__ src = D.src;
-    const PhiloxKey key = D.key;
+    const InstView V = item_view<kOne>(L, one, item, ii, j);
+    const uint32_t *__restrict__ off = V.off;
+    const uint32_t *__restrict__ rthr = V.rthr;
+    const uint32_t *__restrict__ thr = V.thr;
+    const uint32_t *__restrict__ src = V.src;
+    const PhiloxKey key = V.key;
     const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
 
     if (++epoch == 0xFFFFFFFFu) {              // epochs ran out: wipe the table once
@@ -251,7 +283,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
       __syncwarp();
       epoch = 1;
     }
-    const uint32_t root = draw_root(key, j, D.n);
+    const uint32_t root = draw_root(key, j, V.n);
     if (lane == 0) {
       q[0] = root;
       ht[(root * 0x9E3779B1u) >> (32 - kHashBits)] = ((unsigned long long)epoch << 32) | root;
@@ -303,7 +335,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
       if (lane == 0) defer(L, ii, j);
       continue;
     }
-    commit_warp(L, ii, j, q, tail, nullptr);
+    commit_warp(L, V, ii, j, q, tail, nullptr);
   }
   if (lane == 0) cs.epoch[worker] = epoch;
 }
@@ -341,7 +373,8 @@ __device__ __forceinline__ void block_flush(const uint32_t *__restrict__ src, co
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, BigScratch bs) {
+template <bool kOne>
+__global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, BigScratch bs, InstDesc one) {
   __shared__ uint32_t cand_all[kBigWarps][kBigCand];
   __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
   __shared__ uint32_t w_tot[kBigWarps];
@@ -359,16 +392,15 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
     if (item >= L.total_items) break;
     uint32_t ii;
     uint64_t j;
-    decode_item(L, item, ii, j);
-    const InstDesc &D = L.inst[ii];
-    const uint32_t *__restrict__ off = D.off;
-    const uint32_t *__restrict__ rthr = D.rthr;
-    const uint32_t *__restrict__ thr = D.thr;
-    const uint32_t *__restrict__ src = D.src;
-    const PhiloxKey key = D.key;
+    const InstView V = item_view<kOne>(L, one, item, ii, j);
+    const uint32_t *__restrict__ off = V.off;
+    const uint32_t *__restrict__ rthr = V.rthr;
+    const uint32_t *__restrict__ thr = V.thr;
+    const uint32_t *__restrict__ src = V.src;
+    const PhiloxKey key = V.key;
     const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
     if (tid == 0) {
-      const uint32_t root = draw_root(key, j, D.n);
+      const uint32_t root = draw_root(key, j, V.n);
       q[0] = root;
       bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
       s_head = 0;
@@ -450,19 +482,19 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
     if (tid == 0) s_base = atomicAdd(&L.inst[ii].store_tail, (unsigned long long)size);
     __syncthreads();
     const unsigned long long base = s_base;
-    const bool fits = base + size <= D.store_cap;
+    const bool fits = base + size <= V.store_cap;
     for (uint32_t i = tid; i < size; i += kBigBlock) {
       const uint32_t x = q[i];
       if (fits) {
-        D.members[base + i] = x;
-        atomicAdd(&D.cnt[x], 1u);
+        V.members[base + i] = x;
+        atomicAdd(&V.cnt[x], 1u);
       }
       bm[x >> 5] = 0u;
     }
     if (tid == 0) {
       if (fits) {
-        D.rr_start[j] = base;
-        D.rr_len[j] = size;
+        V.rr_start[j] = base;
+        V.rr_len[j] = size;
         atomicAdd(&L.inst[ii].members_added, (unsigned long long)size);
       } else {
         defer(L, ii, j);
@@ -522,13 +554,13 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     if (lane == 0) decode_item(L, item, ii, j);
     ii = __shfl_sync(kFullMask, ii, 0);
     j = __shfl_sync(kFullMask, j, 0);
-    const InstDesc &D = L.inst[ii];
-    const uint32_t *__restrict__ off = D.off;
-    const uint64_t *__restrict__ cum = D.cum;
-    const uint32_t *__restrict__ src = D.src;
-    const PhiloxKey key = D.key;
+    const InstView V = view_of(L.inst[ii]);
+    const uint32_t *__restrict__ off = V.off;
+    const uint64_t *__restrict__ cum = V.cum;
+    const uint32_t *__restrict__ src = V.src;
+    const PhiloxKey key = V.key;
     const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
-    uint32_t x = draw_root(key, j, D.n);
+    uint32_t x = draw_root(key, j, V.n);
     if (lane == 0) {
       path[0] = x;
       if (kLarge) bm[x >> 5] = 1u << (x & 31u);
@@ -572,7 +604,7 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
       if (lane == 0) defer(L, ii, j);
       continue;
     }
-    commit_warp(L, ii, j, path, len, bm);
+    commit_warp(L, V, ii, j, path, len, bm);
     __syncwarp();
   }
 }
@@ -614,7 +646,7 @@ __global__ void __launch_bounds__(256) philox_rate_kernel(PhiloxKey key, uint32_
 
 int ic_common_blocks_per_sm() {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ic_common_kernel, 256, 0) != cudaSuccess) b = 4;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ic_common_kernel<false>, 256, 0) != cudaSuccess) b = 4;
   return b > 0 ? b : 1;
 }
 
@@ -625,13 +657,20 @@ int lt_common_blocks_per_sm() {
   return b > 0 ? b : 1;
 }
 
-cudaError_t launch_ic_common(const SampleLaunch &L, const CommonScratch &cs, cudaStream_t s) {
-  ic_common_kernel<<<(cs.workers + 7) / 8, 256, 0, s>>>(L, cs);
+cudaError_t launch_ic_common(const SampleLaunch &L, const CommonScratch &cs, const InstDesc *one, cudaStream_t s) {
+  if (one)
+    ic_common_kernel<true><<<(cs.workers + 7) / 8, 256, 0, s>>>(L, cs, *one);
+  else
+    ic_common_kernel<false><<<(cs.workers + 7) / 8, 256, 0, s>>>(L, cs, InstDesc{});
   return cudaGetLastError();
 }
 
-cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s) {
-  ic_block_kernel<<<grid, kBigBlock, 0, s>>>(L, bs);
+cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, const InstDesc *one,
+                            cudaStream_t s) {
+  if (one)
+    ic_block_kernel<true><<<grid, kBigBlock, 0, s>>>(L, bs, *one);
+  else
+    ic_block_kernel<false><<<grid, kBigBlock, 0, s>>>(L, bs, InstDesc{});
   return cudaGetLastError();
 }
 
