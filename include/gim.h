@@ -179,6 +179,46 @@ gim_status gim_select_seeds_noalloc(uint32_t n, uint64_t num_sets, uint64_t num_
                                     uint32_t *d_seeds_out, uint32_t *d_gains_out, uint64_t *d_covered_out,
                                     void *stream, char *msg, size_t msg_len);
 
+/* Parameters of one IMM instance of a batch (as the arguments of gim_imm). */
+typedef struct {
+  gim_model model;
+  uint32_t k;
+  double eps;
+  double ell;
+  uint64_t seed;
+} gim_imm_params;
+
+/* Outcome of one IMM instance of a batch. */
+typedef struct {
+  uint64_t theta;       /* final theta = ceil(lambda* / LB)                  */
+  double lb;            /* the lower bound LB of Alg. 2 (1 if never raised)  */
+  uint64_t rr_count;    /* |R| at the end                                    */
+  uint32_t lb_rounds;   /* lower-bound rounds run                            */
+  gim_status status;    /* GIM_OK                                            */
+} gim_imm_result;
+
+/*
+ * Batched IMM: runs gim_imm's algorithm (Alg. 2 then Alg. 1) on n_inst
+ * contexts at once, instance i on ctxs[i]'s graph with params[i]. The
+ * instances advance in lockstep: each round, the RR sets every unfinished
+ * instance still needs are drawn in one launch per diffusion model whose
+ * device work queue holds (instance, rr_id) items, and the greedy selections
+ * of all unfinished instances run as one replay of a CUDA graph of
+ * multi-instance kernels. Instance i's seeds, theta, LB and final RR
+ * collection are exactly those gim_imm(ctxs[i], params[i]...) gives.
+ *   ctxs:      n_inst distinct contexts of one device, each with a graph;
+ *              the work is issued on ctxs[0]'s stream.
+ *   params:    n_inst entries (validated as in gim_imm).
+ *   seeds_out: n_inst host pointers, seeds_out[i] holding params[i].k entries.
+ *   results:   n_inst entries.
+ * Errors: GIM_ERR_ARG (n_inst = 0, a repeated or null context, contexts on
+ * different devices, a parameter gim_imm would reject), GIM_ERR_STATE (a
+ * context without a graph), GIM_ERR_OOM, GIM_ERR_CUDA; the description is
+ * on ctxs[0] (gim_last_error_string).
+ */
+gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params,
+                         uint32_t *const *seeds_out, gim_imm_result *results);
+
 /* ---- introspection (tests, tools) ------------------------------------- */
 
 /* *count_out = |R|; *members_out (nullable) = total members over all sets. */

@@ -29,6 +29,16 @@ _c_f32p = ctypes.POINTER(ctypes.c_float)
 _c_f64p = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
 
+class ImmParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("k", ctypes.c_uint32), ("eps", ctypes.c_double), ("ell", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class ImmResult(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_uint64), ("lb", ctypes.c_double), ("rr_count", ctypes.c_uint64),
+                ("lb_rounds", ctypes.c_uint32), ("status", ctypes.c_int)]
+
+
 # name -> (restype, argtypes), mirroring include/gim.h
 SIGNATURES = {
     "gim_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
@@ -40,6 +50,8 @@ SIGNATURES = {
     "gim_select_seeds": (ctypes.c_int, [_vp, ctypes.c_uint32, _c_u32p, _c_u64p, _c_u32p]),
     "gim_imm": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                ctypes.c_uint64, _c_u32p, _c_u64p, _c_f64p]),
+    "gim_batch_imm": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.POINTER(ImmParams),
+                                     ctypes.POINTER(_c_u32p), ctypes.POINTER(ImmResult)]),
     "gim_rr_count": (ctypes.c_int, [_vp, _c_u64p, _c_u64p]),
     "gim_rr_export": (ctypes.c_int, [_vp, _c_u64p, _c_u32p]),
     "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
@@ -213,3 +225,22 @@ def select_seeds_noalloc(n: int, num_sets: int, num_members: int, d_offsets: int
                                     _vp(stream) if stream else None, buf, 256)
     if st != 0:
         raise GimError(st, "gim_select_seeds_noalloc: " + buf.value.decode())
+
+
+def batch_imm(contexts, params):
+    """gim_batch_imm over Context objects; params: list of (model, k, eps, ell, seed).
+
+    Returns one dict per instance (seeds, theta, lb, rr_count, lb_rounds)."""
+    L = load_library()
+    n = len(contexts)
+    hs = (_vp * n)(*[c.h for c in contexts])
+    ps = (ImmParams * n)(*[ImmParams(int(m), int(k), float(e), float(l), int(sd)) for (m, k, e, l, sd) in params])
+    seeds = [np.zeros(int(p[1]), np.uint32) for p in params]
+    sp = (_c_u32p * n)(*[_p(a, _c_u32p) for a in seeds])
+    rs = (ImmResult * n)()
+    st = L.gim_batch_imm(hs, n, ps, sp, rs)
+    if st != 0:
+        msg = L.gim_last_error_string(contexts[0].h)
+        raise GimError(st, "gim_batch_imm: " + (msg.decode() if msg else ""))
+    return [dict(seeds=seeds[i], theta=int(rs[i].theta), lb=float(rs[i].lb), rr_count=int(rs[i].rr_count),
+                 lb_rounds=int(rs[i].lb_rounds)) for i in range(n)]

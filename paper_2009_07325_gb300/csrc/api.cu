@@ -80,30 +80,6 @@ gim_status do_select(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *co
   return GIM_OK;
 }
 
-// IMM constants (Tang, Shi, Xiao 2015) in a fixed evaluation order.
-struct ImmConst {
-  double ellp, epsp, lam1, lam2;
-  int i_max;
-};
-
-ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell) {
-  ImmConst c;
-  const double logn = std::log((double)n);
-  c.ellp = ell * (1.0 + std::log(2.0) / logn);
-  c.epsp = std::sqrt(2.0) * eps;
-  double lnc = 0.0;
-  for (uint32_t i = 0; i < k; ++i) lnc += std::log((double)(n - i)) - std::log((double)(i + 1));
-  c.lam1 = (2.0 + 2.0 * c.epsp / 3.0) * (lnc + c.ellp * logn + std::log(std::log2((double)n))) * (double)n /
-           (c.epsp * c.epsp);
-  const double g = 1.0 - std::exp(-1.0);
-  const double alpha = std::sqrt(c.ellp * logn + std::log(2.0));
-  const double beta = std::sqrt(g * (lnc + c.ellp * logn + std::log(2.0)));
-  const double t = g * alpha + beta;
-  c.lam2 = 2.0 * (double)n * t * t / (eps * eps);
-  c.i_max = (31 - __builtin_clz(n)) - 1;
-  return c;
-}
-
 }  // namespace
 
 // ===========================================================================
@@ -370,6 +346,31 @@ gim_status gim_imm(gim_ctx *ctx, gim_model model, uint32_t k, double eps, double
   ctx->t_wall_ms = ms_since(t0);
   ctx->lb_rounds = rounds;
   return GIM_OK;
+}
+
+gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params,
+                         uint32_t *const *seeds_out, gim_imm_result *results) {
+  if (!ctxs || n_inst == 0 || !ctxs[0]) return GIM_ERR_ARG;
+  gim_ctx *ctx = ctxs[0];
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!params || !seeds_out || !results) return set_err(ctx, GIM_ERR_ARG, "null argument array");
+  std::vector<gim_ctx *> seen(ctxs, ctxs + n_inst);
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end() || !seen[0])
+    return set_err(ctx, GIM_ERR_ARG, "contexts must be distinct and non-null");
+  for (uint32_t i = 0; i < n_inst; ++i) {
+    gim_ctx *c = ctxs[i];
+    const gim_imm_params &p = params[i];
+    if (c->device != ctx->device) return set_err(ctx, GIM_ERR_ARG, "instance %u: context on another device", i);
+    if (!c->has_graph) return set_err(ctx, GIM_ERR_STATE, "instance %u: no graph loaded", i);
+    if (p.model != GIM_IC && p.model != GIM_LT) return set_err(ctx, GIM_ERR_ARG, "instance %u: unknown model", i);
+    if (p.k == 0 || p.k > c->g.n || !seeds_out[i]) return set_err(ctx, GIM_ERR_ARG, "instance %u: bad k or seeds", i);
+    if (!(p.eps > 0.0 && p.eps < 1.0)) return set_err(ctx, GIM_ERR_ARG, "instance %u: eps not in (0, 1)", i);
+    if (!(p.ell > 0.0)) return set_err(ctx, GIM_ERR_ARG, "instance %u: ell <= 0", i);
+    if (p.model == GIM_LT && !c->lt_ok) return set_err(ctx, GIM_ERR_ARG, "instance %u: graph not LT-valid", i);
+  }
+  return batch_imm(ctxs, n_inst, params, seeds_out, results);
 }
 
 gim_status gim_rr_count(gim_ctx *ctx, uint64_t *count_out, uint64_t *members_out) {

@@ -2,6 +2,7 @@
 // of sampling jobs (one or many contexts per launch), including the
 // large-set passes and on-demand growth of the RR stores.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -77,6 +78,26 @@ template cudaError_t grow_copy<uint32_t>(uint32_t *&, uint64_t &, uint64_t, uint
 template cudaError_t grow_copy<uint64_t>(uint64_t *&, uint64_t &, uint64_t, uint64_t, cudaStream_t);
 template cudaError_t grow_copy<unsigned long long>(unsigned long long *&, uint64_t &, uint64_t, uint64_t,
                                                    cudaStream_t);
+
+// IMM constants (Tang, Shi, Xiao 2015) in a fixed evaluation order.
+ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell) {
+  ImmConst c;
+  const double logn = std::log((double)n);
+  c.ellp = ell * (1.0 + std::log(2.0) / logn);
+  c.epsp = std::sqrt(2.0) * eps;
+  double lnc = 0.0;
+  for (uint32_t i = 0; i < k; ++i) lnc += std::log((double)(n - i)) - std::log((double)(i + 1));
+  c.lam1 = (2.0 + 2.0 * c.epsp / 3.0) * (lnc + c.ellp * logn + std::log(std::log2((double)n))) * (double)n /
+           (c.epsp * c.epsp);
+  const double g = 1.0 - std::exp(-1.0);
+  const double alpha = std::sqrt(c.ellp * logn + std::log(2.0));
+  const double beta = std::sqrt(g * (lnc + c.ellp * logn + std::log(2.0)));
+  const double t = g * alpha + beta;
+  c.lam2 = 2.0 * (double)n * t * t / (eps * eps);
+  c.i_max = (31 - __builtin_clz(n)) - 1;
+  return c;
+}
+
 
 DeviceShared &device_shared(int device) { return g_shared[device]; }
 

@@ -212,13 +212,25 @@ struct SampleJobH {
   uint64_t count;
 };
 
+// IMM constants (Tang, Shi, Xiao 2015): ell', eps', lambda', lambda*, and
+// the number of lower-bound rounds floor(log2 n) - 1.
+struct ImmConst {
+  double ellp, epsp, lam1, lam2;
+  int i_max;
+};
+
 // engine.cu
+ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell);
 gim_status set_err(gim_ctx *ctx, gim_status st, const char *fmt, ...);
 gim_status cuda_err(gim_ctx *ctx, cudaError_t e, const char *what);
 gim_status shared_acquire(gim_ctx *ctx);
 void shared_release(int device);
 DeviceShared &device_shared(int device);
 gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s);
+
+// batch.cu
+gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint32_t *const *seeds_out,
+                     gim_imm_result *results);
 template <typename T>
 cudaError_t grow_copy(T *&p, uint64_t &cap, uint64_t need, uint64_t keep, cudaStream_t s);
 

@@ -1,0 +1,77 @@
+"""Batched IMM (gim_batch_imm) against one-at-a-time gim_imm and the oracle.
+
+A batch of instances with different graphs (Erdos-Renyi, Chung-Lu power
+law, a 3-vertex graph whose lower-bound search has no round), diffusion
+models (IC and LT), k, eps and seeds must give every instance exactly the
+seeds, theta, LB and RR collection it gets alone.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context, GimError
+from paper_2009_07325_gb300 import binding
+from paper_2009_07325_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, O.max_threads())
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2009_07325_gb300 import build
+    build.build()
+
+
+def _graphs():
+    three = I.from_edges(3, [0, 1, 2, 0], [1, 2, 0, 2]).with_weights(np.array([0.5, 0.5, 0.5, 0.4], np.float32), "three")
+    return [
+        (I.wc_weights(I.er(2000, 20000, 1)), (GIM_IC, 10, 0.5, 1.0, 7)),
+        (I.wc_weights(I.chung_lu(12000, 11)), (GIM_IC, 25, 0.2, 1.0, 1011)),
+        (I.wc_weights(I.chung_lu(30000, 12)), (GIM_LT, 10, 0.3, 1.0, 1012)),
+        (I.wc_weights(I.er(500, 3000, 4)), (GIM_LT, 50, 0.5, 1.0, 3)),
+        (I.wc_weights(I.chung_lu(20000, 13)), (GIM_IC, 50, 0.5, 1.0, 1013)),
+        (three, (GIM_IC, 1, 0.5, 1.0, 9)),
+    ]
+
+
+def test_batch_matches_single_runs_and_oracle():
+    cases = _graphs()
+    ctxs = []
+    for g, _ in cases:
+        c = Context(0)
+        c.load(g)
+        ctxs.append(c)
+    res = binding.batch_imm(ctxs, [p for _, p in cases])
+    for (g, p), c, r in zip(cases, ctxs, res):
+        alone = Context(0)
+        alone.load(g)
+        a = alone.imm(*p)
+        assert r["seeds"].tolist() == a["seeds"].tolist(), p
+        assert (r["theta"], r["lb"], r["rr_count"]) == (a["theta"], a["lb"], a["rr_count"]), p
+        ob, mb = c.rr_export()
+        oa, ma = alone.rr_export()
+        assert np.array_equal(ob, oa) and np.array_equal(mb, ma)
+        o = O.Oracle(g).imm(p[0], p[1], p[2], p[3], p[4], THREADS)
+        assert r["seeds"].tolist() == o["seeds"].tolist() and r["theta"] == o["theta"] and r["lb"] == o["lb"]
+        assert r["lb_rounds"] == len(o["rounds"])
+
+
+def test_batch_twice_in_a_row_and_errors():
+    g = I.wc_weights(I.er(1000, 8000, 2))
+    a, b = Context(0), Context(0)
+    a.load(g)
+    b.load(g)
+    p = [(GIM_IC, 5, 0.4, 1.0, 1), (GIM_LT, 7, 0.4, 1.0, 2)]
+    r1 = binding.batch_imm([a, b], p)
+    r2 = binding.batch_imm([a, b], p)
+    for x, y in zip(r1, r2):
+        assert x["seeds"].tolist() == y["seeds"].tolist() and x["theta"] == y["theta"]
+    with pytest.raises(GimError):
+        binding.batch_imm([a, a], p)                   # repeated context
+    with pytest.raises(GimError):
+        binding.batch_imm([a, b], [(GIM_IC, 5, 1.5, 1.0, 1), p[1]])   # bad eps
+    bad = Context(0)
+    bad.load(I.uniform_weights(I.er(100, 900, 1), 0.9))   # not LT-valid
+    with pytest.raises(GimError):
+        binding.batch_imm([a, bad], [p[0], (GIM_LT, 3, 0.5, 1.0, 1)])
