@@ -50,7 +50,106 @@ WORKLOADS = {
                              weights="weighted cascade 1/indeg(v) fp32", model="IC", k=10, eps=0.5, ell=1.0,
                              philox_seed=7),
 }
+WORKLOADS["batch-chunglu-256"] = dict(
+    graph="256 Chung-Lu graphs (degree exponent 2.1, 8n draws, dedup), n = round(10^(4+2U)), graph seed 1000+i",
+    weights="weighted cascade 1/indeg(v) fp32", model="IC", k="from {10,25,50}", eps="from {0.1,0.2,0.5}", ell=1.0,
+    philox_seed="1000+i", instances=256)
 WORKLOAD = dict(workload="imm-ic-wc-rmat22", **WORKLOADS["imm-ic-wc-rmat22"])
+
+
+def batch_instances(count=256):
+    """The batched workload: per instance (graph, (model, k, eps, ell, seed))."""
+    from paper_2009_07325_gb300 import GIM_IC
+    from paper_2009_07325_gb300 import inputs as I
+    r = I.u64_stream(4, 900, 3 * count)
+    out = []
+    for i in range(count):
+        u = float(r[3 * i] >> np.uint64(11)) * 2.0 ** -53
+        n = int(round(10 ** (4 + 2 * u)))
+        k = (10, 25, 50)[int(r[3 * i + 1] % np.uint64(3))]
+        eps = (0.1, 0.2, 0.5)[int(r[3 * i + 2] % np.uint64(3))]
+        out.append((n, (GIM_IC, k, eps, 1.0, 1000 + i)))
+    return out
+
+
+def run_batch(args):
+    """Batched IMM (gim_batch_imm over all instances) against the same
+    instances run one after another with gim_imm, graphs resident."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07325_gb300 import Context, binding
+    from paper_2009_07325_gb300 import inputs as I
+    specs = batch_instances(WORKLOAD["instances"])
+    t0 = time.perf_counter()
+    graphs = [I.wc_weights(I.chung_lu(n, 1000 + i)) for i, (n, _) in enumerate(specs)]
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=local)
+    ctxs = []
+    for g in graphs:
+        c = Context(local, stream=stream.cuda_stream)
+        c.load(g)
+        ctxs.append(c)
+    params = [p for _, p in specs]
+    batch_budget, _ = binding.autotune(ctxs, params, 2000)        # schedule for the batch as a whole
+    for _ in range(max(1, args.warmup)):
+        res = binding.batch_imm(ctxs, params)
+    ctxs[0].reset_timings()
+    launches0 = ctxs[0].launch_count()
+    torch.cuda.synchronize()
+    bt = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            res = binding.batch_imm(ctxs, params)
+            torch.cuda.synchronize()
+            bt.append(time.perf_counter() - t1)
+    launches = ctxs[0].launch_count() - launches0
+    tb = ctxs[0].timings()                        # host-side phase split of the last batch
+    batched_seeds = [r["seeds"].tolist() for r in res]
+    # the plain path: one gim_imm per instance, back to back, each instance
+    # with the schedule the autotuner picks for it alone (one warm-up pass)
+    plain_budgets = [binding.autotune([c], [p], 2000)[0] for c, p in zip(ctxs, params)]
+    for c, p in zip(ctxs, params):
+        c.imm(*p)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for c in ctxs:
+        c.reset_timings()
+    plain, p_sample, p_select = [], 0.0, 0.0
+    for c, p in zip(ctxs, params):
+        plain.append(c.imm(*p))
+        tp = c.timings()
+        p_sample += tp["sample_ms"]
+        p_select += tp["select_ms"]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t1
+    same = all(a == b["seeds"].tolist() for a, b in zip(batched_seeds, plain))
+    t_b = float(np.median(bt))
+    units, secs = aggregate(float(len(ctxs)) * args.steps, sum(bt))
+    line = {"metric": "batched IMM queries/s (256 Chung-Lu instances, IC-WC)", "value": units / secs,
+            "unit": "IMM-instances/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": dict(WORKLOAD),
+            "batched_s": t_b, "plain_sequential_s": t_plain, "speedup_vs_plain": t_plain / t_b,
+            "identical_seed_sets": same, "rr_sets": sum(r["rr_count"] for r in res),
+            "batched_split_ms": {"sample": tb["sample_ms"], "select": tb["select_ms"], "wall": tb["wall_ms"]},
+            "plain_split_ms": {"sample": p_sample, "select": p_select,
+                               "common_kernel": sum(c.timings()["kernel_ms"] for c in ctxs),
+                               "large_kernel": sum(c.timings()["large_ms"] for c in ctxs)},
+            "batched_kernel_ms_per_batch": {"common": tb["kernel_ms"] / args.steps,
+                                            "large": tb["large_ms"] / args.steps},
+            "rounds": max(r["lb_rounds"] for r in res) + 1,
+            "tuning": {"batch_group_budget": batch_budget,
+                       "plain_group_budgets": sorted(set(plain_budgets)), "by": "gim_autotune"},
+            "gpu_launches": launches, "graph_generation_s": t_gen, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    return 0
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -272,6 +371,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=f"cuda:{local}")
 
     mdl = model_id()
+    from paper_2009_07325_gb300 import binding
+    budget, _ = binding.autotune([ctx], [(mdl, k, eps, ell, seed)], 20000)   # schedule for this profile
     for _ in range(args.warmup):
         ctx.imm(mdl, k, eps, ell, seed)
 
@@ -340,6 +441,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas{world}", l2="flushed between steps (512 MiB write)"),
             "imm_s": secs / args.steps, "theta": thetas[-1], "rr_sets_per_step": rr_sets / args.steps,
+            "tuning": {"group_budget": budget, "by": "gim_autotune"},
             "sample_ms_per_step": sample_ms / args.steps, "select_ms_per_step": select_ms / args.steps,
             "e2e": {"value": e2e_u / e2e_s, "unit": "RR-sets/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3))},
@@ -406,6 +508,8 @@ def main():
     WORKLOAD.update(workload=args.workload, **WORKLOADS[args.workload])
     if args.case:
         return run_case(args)
+    if args.workload.startswith("batch-") and args.impl == "ours":
+        return run_batch(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -219,6 +219,36 @@ typedef struct {
 gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params,
                          uint32_t *const *seeds_out, gim_imm_result *results);
 
+/* Tuning knobs of a context (they change speed, never results). */
+typedef enum {
+  /* In-edge groups (4 in-edges each) one RR set may scan in the warp-per-set
+     IC pass before it is handed to the block-per-set pass. Default 16384. */
+  GIM_OPT_GROUP_BUDGET = 0
+} gim_option;
+
+/* Sets a tuning knob. Errors: GIM_ERR_ARG (unknown option or value 0). */
+gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value);
+
+/* Reads a tuning knob into *value. */
+gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value);
+
+/*
+ * Autotuner: picks GIM_OPT_GROUP_BUDGET - how long one warp keeps an RR set
+ * before a 512-thread block takes it over, i.e. warps per RR set for heavy
+ * sets - for a workload, by timing the sampling of `sample_sets` RR sets
+ * per instance under each candidate (4096 .. 2^30 groups) exactly as
+ * gim_batch_imm (n_inst > 1) or gim_imm (n_inst = 1) would launch it. The
+ * choice is cached for the process under the workload's degree profile
+ * (log2 of n, of mean and of maximum in-degree, the model, log2 of n_inst),
+ * so later calls with the same profile only read the cache. The chosen value
+ * is set on every context; their RR collections are emptied.
+ *   ctxs, n_inst, params: as for gim_batch_imm (params give model and seed).
+ *   budget_out: nullable; the chosen budget. measured_out: nullable; 1 if
+ *   this call timed the candidates, 0 if it used the cache.
+ */
+gim_status gim_autotune(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params, uint64_t sample_sets,
+                        uint64_t *budget_out, int *measured_out);
+
 /* ---- introspection (tests, tools) ------------------------------------- */
 
 /* *count_out = |R|; *members_out (nullable) = total members over all sets. */

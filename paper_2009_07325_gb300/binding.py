@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgim.so")
 
 GIM_IC, GIM_LT = 0, 1
+GIM_OPT_GROUP_BUDGET = 0
 STATUS = {0: "GIM_OK", 1: "GIM_ERR_ARG", 2: "GIM_ERR_OOM", 3: "GIM_ERR_CUDA", 4: "GIM_ERR_TIMEOUT",
           5: "GIM_ERR_STATE"}
 
@@ -52,6 +53,10 @@ SIGNATURES = {
                                ctypes.c_uint64, _c_u32p, _c_u64p, _c_f64p]),
     "gim_batch_imm": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.POINTER(ImmParams),
                                      ctypes.POINTER(_c_u32p), ctypes.POINTER(ImmResult)]),
+    "gim_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint64]),
+    "gim_get_option": (ctypes.c_int, [_vp, ctypes.c_int, _c_u64p]),
+    "gim_autotune": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.POINTER(ImmParams),
+                                    ctypes.c_uint64, _c_u64p, ctypes.POINTER(ctypes.c_int)]),
     "gim_rr_count": (ctypes.c_int, [_vp, _c_u64p, _c_u64p]),
     "gim_rr_export": (ctypes.c_int, [_vp, _c_u64p, _c_u32p]),
     "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
@@ -205,6 +210,14 @@ class Context:
         self._check(self.L.gim_diag_philox_rate(self.h, ctypes.byref(out)), "gim_diag_philox_rate")
         return float(out.value)
 
+    def set_option(self, opt: int, value: int):
+        self._check(self.L.gim_set_option(self.h, opt, value), "gim_set_option")
+
+    def get_option(self, opt: int) -> int:
+        v = ctypes.c_uint64(0)
+        self._check(self.L.gim_get_option(self.h, opt, ctypes.byref(v)), "gim_get_option")
+        return int(v.value)
+
     def launch_count(self) -> int:
         c = ctypes.c_uint64(0)
         self._check(self.L.gim_launch_count(self.h, ctypes.byref(c)), "gim_launch_count")
@@ -244,3 +257,18 @@ def batch_imm(contexts, params):
         raise GimError(st, "gim_batch_imm: " + (msg.decode() if msg else ""))
     return [dict(seeds=seeds[i], theta=int(rs[i].theta), lb=float(rs[i].lb), rr_count=int(rs[i].rr_count),
                  lb_rounds=int(rs[i].lb_rounds)) for i in range(n)]
+
+
+def autotune(contexts, params, sample_sets: int = 2000):
+    """gim_autotune: choose the sampling schedule for these contexts; returns (budget, measured)."""
+    L = load_library()
+    n = len(contexts)
+    hs = (_vp * n)(*[c.h for c in contexts])
+    ps = (ImmParams * n)(*[ImmParams(int(m), int(k), float(e), float(l), int(sd)) for (m, k, e, l, sd) in params])
+    budget = ctypes.c_uint64(0)
+    measured = ctypes.c_int(0)
+    st = L.gim_autotune(hs, n, ps, sample_sets, ctypes.byref(budget), ctypes.byref(measured))
+    if st != 0:
+        msg = L.gim_last_error_string(contexts[0].h)
+        raise GimError(st, "gim_autotune: " + (msg.decode() if msg else ""))
+    return int(budget.value), bool(measured.value)

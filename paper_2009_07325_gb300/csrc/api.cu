@@ -148,10 +148,12 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   if (!in_offsets || (m > 0 && (!in_sources || !in_weights))) return set_err(ctx, GIM_ERR_ARG, "null input array");
   if (in_offsets[0] != 0 || in_offsets[n] != m) return set_err(ctx, GIM_ERR_ARG, "offsets must start at 0 and end at m");
   std::vector<uint32_t> off32((size_t)n + 1);
+  uint32_t max_indeg = 0;
   for (uint64_t v = 0; v <= n; ++v) {
     if (v > 0 && in_offsets[v] < in_offsets[v - 1]) return set_err(ctx, GIM_ERR_ARG, "offsets decrease at row %llu",
                                                                    (unsigned long long)v - 1);
     off32[v] = (uint32_t)in_offsets[v];
+    if (v > 0) max_indeg = std::max<uint32_t>(max_indeg, off32[v] - off32[v - 1]);
   }
   const uint64_t m_pad = (m + 3) / 4 * 4 + 4;
   DevGraph g;
@@ -204,6 +206,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   ctx->g = g;
   ctx->has_graph = true;
   ctx->lt_ok = (flags & kGraphNotLT) ? 0 : 1;
+  ctx->max_indeg = max_indeg;
   dfree(ctx->st.cnt);
   free_select(ctx->sel);
   ctx->R = ctx->Z = ctx->store_used = 0;
@@ -371,6 +374,38 @@ gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_pa
     if (p.model == GIM_LT && !c->lt_ok) return set_err(ctx, GIM_ERR_ARG, "instance %u: graph not LT-valid", i);
   }
   return batch_imm(ctxs, n_inst, params, seeds_out, results);
+}
+
+gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value) {
+  if (!ctx) return GIM_ERR_ARG;
+  if (opt == GIM_OPT_GROUP_BUDGET && value > 0) {
+    ctx->group_budget = (uint32_t)std::min<uint64_t>(value, 0xFFFFFFFEull);
+    return GIM_OK;
+  }
+  return set_err(ctx, GIM_ERR_ARG, "unknown option or zero value");
+}
+
+gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value) {
+  if (!ctx || !value) return GIM_ERR_ARG;
+  if (opt == GIM_OPT_GROUP_BUDGET) {
+    *value = ctx->group_budget;
+    return GIM_OK;
+  }
+  return set_err(ctx, GIM_ERR_ARG, "unknown option");
+}
+
+gim_status gim_autotune(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params, uint64_t sample_sets,
+                        uint64_t *budget_out, int *measured_out) {
+  if (!ctxs || n_inst == 0 || !ctxs[0] || !params) return GIM_ERR_ARG;
+  gim_ctx *ctx = ctxs[0];
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  for (uint32_t i = 0; i < n_inst; ++i) {
+    if (!ctxs[i] || ctxs[i]->device != ctx->device) return set_err(ctx, GIM_ERR_ARG, "instance %u: bad context", i);
+    if (!ctxs[i]->has_graph) return set_err(ctx, GIM_ERR_STATE, "instance %u: no graph loaded", i);
+    if (params[i].model == GIM_LT && !ctxs[i]->lt_ok) return set_err(ctx, GIM_ERR_ARG, "instance %u: not LT-valid", i);
+  }
+  return autotune(ctxs, n_inst, params, sample_sets == 0 ? 2000 : sample_sets, budget_out, measured_out);
 }
 
 gim_status gim_rr_count(gim_ctx *ctx, uint64_t *count_out, uint64_t *members_out) {

@@ -432,9 +432,13 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
       b.n_cap = std::min(c0, std::min(c1, c2));
       CU(ensure_buf(b.inv, b.z_cap, std::max<uint64_t>(c->Z, 1)));
       CU(ensure_buf(b.covered, b.r_cap, std::max<uint64_t>(c->R, 1)));
-      uint64_t k0 = b.k_cap;
-      CU(ensure_buf(b.best, k0, D.k));
-      b.k_cap = k0;
+      if (b.k_cap < D.k || !b.best || !b.seeds || !b.gains) {   // the three k-sized buffers share k_cap
+        uint64_t k0 = b.k_cap, k1 = b.k_cap, k2 = b.k_cap;
+        CU(ensure_buf(b.best, k0, D.k));
+        CU(ensure_buf(b.seeds, k1, D.k));
+        CU(ensure_buf(b.gains, k2, D.k));
+        b.k_cap = std::min(k0, std::min(k1, k2));
+      }
       CU(ensure_buf(b.scan_tmp, b.scan_cap, (uint64_t)D.tiles + 1));
       D.members = c->st.members;
       D.rr_start = c->st.rr_start;

@@ -38,7 +38,6 @@ namespace {
 
 constexpr uint64_t kBigBudget = 8ull << 30;     // bytes of large-pass scratch (bitmaps + queues)
 constexpr uint64_t kInitialStore = 1ull << 24;  // store entries at first use
-constexpr uint32_t kGroupBudget = 1u << 14;     // common pass: 64K in-edges scanned per set at most
 
 DeviceShared g_shared[kMaxDevices];
 
@@ -256,7 +255,7 @@ gim_status run_one(gim_ctx *ctx, DeviceShared &D, int model, std::vector<SampleJ
   L.deferred = P.out;
   L.deferred_cap = D.def_cap / 2;
   L.ctl = D.d_ctl;
-  L.group_budget = P.large ? 0xFFFFFFFFu : kGroupBudget;
+  L.group_budget = P.large ? 0xFFFFFFFFu : ctx->group_budget;   // the first context's knob serves the launch
   if (used) *used = L;
   CU(cudaEventRecord(ctx->ev[6], s));
   cudaError_t e;

@@ -228,6 +228,10 @@ void shared_release(int device);
 DeviceShared &device_shared(int device);
 gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s);
 
+// tune.cu
+gim_status autotune(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint64_t sample_sets,
+                    uint64_t *budget_out, int *measured_out);
+
 // batch.cu
 gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint32_t *const *seeds_out,
                      gim_imm_result *results);
@@ -247,6 +251,7 @@ struct gim_ctx {
 
   bool has_graph = false;
   int lt_ok = 0;
+  uint32_t max_indeg = 0;         // of the loaded graph (degree profile of the autotuner)
   gim::DevGraph g;
 
   // RR collection
@@ -259,6 +264,7 @@ struct gim_ctx {
   gim::DevStore st;
 
   bool shared_held = false;       // holds a reference on the device's shared scratch
+  uint32_t group_budget = 1u << 14;   // GIM_OPT_GROUP_BUDGET
 
   gim::SelectBuffers sel;
 

@@ -1,0 +1,96 @@
+// Autotuner of the sampling schedule (see gim_autotune in gim.h).
+//
+// The knob is the common IC pass's edge budget: how many in-edge groups one
+// warp scans for an RR set before a 512-thread block takes the set over. A
+// small budget sends heavy sets to the block pass early, which bounds the
+// tail of a launch with few sets (one large graph); a large one keeps them
+// on single warps, which is cheaper per coin when many sets are in flight
+// (batches of instances). The best value depends on the degree profile of
+// the graphs and on how many instances share a launch, so candidates are
+// timed on a short sampling run shaped like the real launches and the
+// winner is cached per profile for the rest of the process.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "gim_internal.cuh"
+
+namespace gim {
+
+namespace {
+
+using Profile = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<Profile, uint32_t> g_tune_cache;
+
+int lg(double x) { return x <= 1.0 ? 0 : (int)std::floor(std::log2(x)); }
+
+Profile profile_of(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params) {
+  double n = 0, m = 0, dmax = 0;
+  for (uint32_t i = 0; i < ni; ++i) {
+    n += ctxs[i]->g.n;
+    m += (double)ctxs[i]->g.m;
+    dmax = std::max<double>(dmax, ctxs[i]->max_indeg);
+  }
+  return Profile{lg(n / ni), lg(m / std::max(n, 1.0)), lg(dmax), (int)params[0].model, lg(ni)};
+}
+
+}  // namespace
+
+gim_status autotune(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint64_t sample_sets,
+                    uint64_t *budget_out, int *measured_out) {
+  gim_ctx *ctx = ctxs[0];
+  const Profile key = profile_of(ctxs, ni, params);
+  uint32_t best = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) best = it->second;
+  }
+  const bool measure = best == 0;
+  if (measure) {
+    static const uint32_t kCand[] = {1u << 12, 1u << 14, 1u << 16, 1u << 18, 1u << 30};
+    double best_ms = 0;
+    for (uint32_t cand : kCand) {
+      double ms = 0;
+      for (int rep = 0; rep < 2; ++rep) {       // the first run warms the graph into L2
+        for (uint32_t i = 0; i < ni; ++i) {
+          ctxs[i]->group_budget = cand;
+          ctxs[i]->R = ctxs[i]->Z = ctxs[i]->store_used = 0;
+          ctxs[i]->model = -1;
+          const cudaError_t e = cudaMemsetAsync(ctxs[i]->st.cnt, 0, (uint64_t)ctxs[i]->g.n * 4, ctx->stream);
+          if (e != cudaSuccess) return cuda_err(ctx, e, "autotune reset");
+        }
+        std::vector<SampleJobH> jobs;
+        for (uint32_t i = 0; i < ni; ++i)
+          jobs.push_back(SampleJobH{ctxs[i], (int)params[i].model, params[i].seed, sample_sets});
+        const double k0 = ctx->t_kernel_ms[0] + ctx->t_kernel_ms[1];
+        const gim_status st = sample_jobs(jobs, ctx->stream);
+        if (st != GIM_OK) return st;
+        ms = ctx->t_kernel_ms[0] + ctx->t_kernel_ms[1] - k0;
+      }
+      if (best == 0 || ms < best_ms) {
+        best = cand;
+        best_ms = ms;
+      }
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  for (uint32_t i = 0; i < ni; ++i) {
+    ctxs[i]->group_budget = best;
+    ctxs[i]->R = ctxs[i]->Z = ctxs[i]->store_used = 0;
+    ctxs[i]->model = -1;
+    const cudaError_t e = cudaMemsetAsync(ctxs[i]->st.cnt, 0, (uint64_t)ctxs[i]->g.n * 4, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "autotune reset");
+  }
+  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "autotune");
+  if (budget_out) *budget_out = best;
+  if (measured_out) *measured_out = measure ? 1 : 0;
+  return GIM_OK;
+}
+
+}  // namespace gim

@@ -67,6 +67,9 @@ def test_batch_twice_in_a_row_and_errors():
     r2 = binding.batch_imm([a, b], p)
     for x, y in zip(r1, r2):
         assert x["seeds"].tolist() == y["seeds"].tolist() and x["theta"] == y["theta"]
+    # the contexts stay usable for the single-query calls after a batch
+    assert a.imm(*p[0])["seeds"].tolist() == r1[0]["seeds"].tolist()
+    assert b.select_seeds(7)[0].tolist() == r1[1]["seeds"].tolist()
     with pytest.raises(GimError):
         binding.batch_imm([a, a], p)                   # repeated context
     with pytest.raises(GimError):
@@ -75,3 +78,40 @@ def test_batch_twice_in_a_row_and_errors():
     bad.load(I.uniform_weights(I.er(100, 900, 1), 0.9))   # not LT-valid
     with pytest.raises(GimError):
         binding.batch_imm([a, bad], [p[0], (GIM_LT, 3, 0.5, 1.0, 1)])
+
+
+def test_schedule_never_changes_results():
+    """The group budget (warps per heavy RR set) changes speed only."""
+    g = I.wc_weights(I.rmat(16, 8))
+    ref = None
+    for budget in (1, 64, 4096, 1 << 30):
+        c = Context(0)
+        c.load(g)
+        c.set_option(binding.GIM_OPT_GROUP_BUDGET, budget)
+        assert c.get_option(binding.GIM_OPT_GROUP_BUDGET) == budget
+        c.sample_rr(GIM_IC, 8000, 5)
+        got = c.rr_export(), c.coverage(), c.select_seeds(20)
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got[0][0], ref[0][0]) and np.array_equal(got[0][1], ref[0][1])
+            assert np.array_equal(got[1], ref[1])
+            assert [x.tolist() if hasattr(x, "tolist") else x for x in got[2]] == \
+                   [x.tolist() if hasattr(x, "tolist") else x for x in ref[2]]
+
+
+def test_autotune_picks_a_candidate_and_caches_it():
+    g = I.wc_weights(I.chung_lu(20000, 5))
+    cs = [Context(0) for _ in range(3)]
+    for c in cs:
+        c.load(g)
+    params = [(GIM_IC, 10, 0.5, 1.0, s) for s in (1, 2, 3)]
+    b1, m1 = binding.autotune(cs, params, 500)
+    b2, m2 = binding.autotune(cs, params, 500)
+    assert b1 in (1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 30) and m1 and b1 == b2 and not m2
+    assert all(c.get_option(binding.GIM_OPT_GROUP_BUDGET) == b1 and c.rr_count() == (0, 0) for c in cs)
+    r = binding.batch_imm(cs, params)
+    for c, p, x in zip(cs, params, r):
+        alone = Context(0)
+        alone.load(g)
+        assert alone.imm(*p)["seeds"].tolist() == x["seeds"].tolist()
