@@ -219,6 +219,49 @@ typedef struct {
 gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params,
                          uint32_t *const *seeds_out, gim_imm_result *results);
 
+/*
+ * Query server over one resident graph: continuous batching with resident
+ * RR stores. Not in the paper; it serves many IMM queries (gim_imm's
+ * algorithm) on the graph loaded in graph_ctx.
+ *
+ * RR set j depends only on (graph, model, seed, j) and an IMM run uses the
+ * first |R| sets of its sequence, so the server keeps one RR store per
+ * (model, seed) on the device and answers each query from the prefix its
+ * run needs: every query's seeds, theta and LB equal those of
+ * gim_imm(model, k, eps, ell, seed) run alone, while RR sets are sampled once
+ * for all queries sharing a (model, seed). A worker thread advances the
+ * admitted queries together, one IMM round at a time (one sampling launch
+ * per model, then one batched greedy selection); queries that arrive
+ * meanwhile wait in a FIFO and are admitted at the next round when one of
+ * max_active slots is free and their projected RR-store bytes (theta times
+ * the mean RR-set size) fit the memory budget.
+ *
+ * gim_server_start: graph_ctx must hold a graph and must not be changed or
+ *   destroyed until gim_server_stop; the server only reads it.
+ *   max_active in [1, 1024] slots; max_k in [1, n] is the largest k a query
+ *   may ask for; mem_budget_bytes = 0 takes 60% of the free device memory.
+ * gim_server_submit: queues one query; *ticket_out identifies it. Errors:
+ *   GIM_ERR_ARG (k > max_k or a parameter gim_imm would reject),
+ *   GIM_ERR_STATE (the server is stopping).
+ * gim_server_poll: *done = 1 once the query finished (waits up to timeout_ms
+ *   for it); then seeds_out (k entries, nullable), result (nullable) and
+ *   latency_ms (submit to finish, nullable) are filled. Returns the query's
+ *   error if it failed.
+ * gim_server_stats: out[8] = {completed queries, rounds, busy ms, sampling
+ *   ms, selection ms, most queries admitted at once, queries waiting,
+ *   RR sets resident in the pools}.
+ * gim_server_stop: lets admitted queries finish, fails the waiting ones with
+ *   GIM_ERR_STATE, frees the server. Submit/poll/stats are thread-safe.
+ */
+typedef struct gim_server gim_server;
+gim_status gim_server_start(gim_server **out, gim_ctx *graph_ctx, uint32_t max_active, uint32_t max_k,
+                            uint64_t mem_budget_bytes);
+gim_status gim_server_submit(gim_server *srv, const gim_imm_params *params, uint64_t *ticket_out);
+gim_status gim_server_poll(gim_server *srv, uint64_t ticket, uint32_t timeout_ms, int *done, uint32_t *seeds_out,
+                           gim_imm_result *result, double *latency_ms);
+gim_status gim_server_stats(gim_server *srv, double out[8]);
+void gim_server_stop(gim_server *srv);
+
 /* Tuning knobs of a context (they change speed, never results). */
 typedef enum {
   /* In-edge groups (4 in-edges each) one RR set may scan in the warp-per-set

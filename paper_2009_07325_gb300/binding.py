@@ -57,6 +57,13 @@ SIGNATURES = {
     "gim_get_option": (ctypes.c_int, [_vp, ctypes.c_int, _c_u64p]),
     "gim_autotune": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.POINTER(ImmParams),
                                     ctypes.c_uint64, _c_u64p, ctypes.POINTER(ctypes.c_int)]),
+    "gim_server_start": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint64]),
+    "gim_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(ImmParams), _c_u64p]),
+    "gim_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int), _c_u32p,
+                                       ctypes.POINTER(ImmResult), _c_f64p]),
+    "gim_server_stats": (ctypes.c_int, [_vp, _c_f64p]),
+    "gim_server_stop": (None, [_vp]),
     "gim_rr_count": (ctypes.c_int, [_vp, _c_u64p, _c_u64p]),
     "gim_rr_export": (ctypes.c_int, [_vp, _c_u64p, _c_u32p]),
     "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
@@ -272,3 +279,69 @@ def autotune(contexts, params, sample_sets: int = 2000):
         msg = L.gim_last_error_string(contexts[0].h)
         raise GimError(st, "gim_autotune: " + (msg.decode() if msg else ""))
     return int(budget.value), bool(measured.value)
+
+
+class Server:
+    """IMM query server over the graph resident in a Context (gim_server_*)."""
+
+    def __init__(self, graph_ctx: Context, max_active: int = 8, max_k: int = 256, mem_budget_bytes: int = 0):
+        self.L = load_library()
+        self.ctx = graph_ctx
+        h = _vp()
+        st = self.L.gim_server_start(ctypes.byref(h), graph_ctx.h, max_active, max_k, mem_budget_bytes)
+        if st != 0:
+            msg = self.L.gim_last_error_string(graph_ctx.h)
+            raise GimError(st, "gim_server_start: " + (msg.decode() if msg else ""))
+        self.h = h
+        self.k = {}
+
+    def submit(self, model: int, k: int, eps: float, ell: float, seed: int) -> int:
+        t = ctypes.c_uint64(0)
+        p = ImmParams(int(model), int(k), float(eps), float(ell), int(seed))
+        st = self.L.gim_server_submit(self.h, ctypes.byref(p), ctypes.byref(t))
+        if st != 0:
+            raise GimError(st, "gim_server_submit")
+        self.k[int(t.value)] = int(k)
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        """None while running, else dict(seeds, theta, lb, rr_count, lb_rounds, latency_ms)."""
+        done = ctypes.c_int(0)
+        seeds = np.zeros(self.k[ticket], np.uint32)
+        res = ImmResult()
+        lat = ctypes.c_double(0)
+        st = self.L.gim_server_poll(self.h, ticket, timeout_ms, ctypes.byref(done), _p(seeds, _c_u32p),
+                                    ctypes.byref(res), ctypes.byref(lat))
+        if st != 0:
+            raise GimError(st, f"gim_server_poll({ticket})")
+        if not done.value:
+            return None
+        return dict(seeds=seeds, theta=int(res.theta), lb=float(res.lb), rr_count=int(res.rr_count),
+                    lb_rounds=int(res.lb_rounds), latency_ms=float(lat.value))
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        import time
+        t0 = time.time()
+        while time.time() - t0 < timeout_s:
+            r = self.poll(ticket, 100)
+            if r is not None:
+                return r
+        raise TimeoutError(f"query {ticket} did not finish in {timeout_s} s")
+
+    def stats(self) -> dict:
+        out = np.zeros(8, np.float64)
+        if self.L.gim_server_stats(self.h, _p(out, _c_f64p)) != 0:
+            raise GimError(1, "gim_server_stats")
+        keys = ["completed", "rounds", "busy_ms", "sample_ms", "select_ms", "peak_active", "waiting", "pool_sets"]
+        return dict(zip(keys, out.tolist()))
+
+    def stop(self):
+        if getattr(self, "h", None):
+            self.L.gim_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

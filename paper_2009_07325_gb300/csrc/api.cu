@@ -46,6 +46,7 @@ void free_select(SelectBuffers &b) {
   dfree(b.gains);
   dfree(b.covered_total);
   dfree(b.scan_tmp);
+  dfree(b.cnt_own);
   b = SelectBuffers{};
 }
 
@@ -124,7 +125,7 @@ void gim_destroy(gim_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  free_graph(ctx->g);
+  if (ctx->owns_graph) free_graph(ctx->g);
   dfree(ctx->st.members);
   dfree(ctx->st.rr_start);
   dfree(ctx->st.rr_len);
@@ -202,7 +203,8 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
 
   // commit: replace the graph and empty the collection
   cudaStreamSynchronize(s);
-  free_graph(ctx->g);
+  if (ctx->owns_graph) free_graph(ctx->g);
+  ctx->owns_graph = true;
   ctx->g = g;
   ctx->has_graph = true;
   ctx->lt_ok = (flags & kGraphNotLT) ? 0 : 1;

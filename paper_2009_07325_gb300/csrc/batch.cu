@@ -32,13 +32,13 @@ constexpr uint32_t kCoverBlocks = 8;    // cover blocks per instance
 
 // One instance of a batched selection. Block ranges are fixed for the batch.
 struct SelDesc {
-  uint32_t n, k, active, pad;
+  uint32_t n, k, active, count_own;       // count_own: cnt is computed here from sets [0, R)
   unsigned long long R;
   unsigned long long set_begin;           // prefix of R over the batch (fill kernel)
   const uint32_t *members;
   const uint64_t *rr_start;
   const uint32_t *rr_len;
-  const uint32_t *cnt;
+  uint32_t *cnt;                          // occurrence counts (written by bsel_count when count_own)
   uint32_t *cnt_work;
   uint64_t *inv_off;
   uint32_t *cursor;
@@ -112,6 +112,33 @@ __global__ void __launch_bounds__(kSelThreads) bsel_clear(const SelDesc *d, uint
     for (uint64_t t = threadIdx.x; t < D.R; t += blockDim.x) D.covered[t] = 0;
     for (uint32_t t = threadIdx.x; t < D.k; t += blockDim.x) D.best[t] = 0ull;
     if (threadIdx.x == 0) *D.covered_total = 0ull;
+  }
+}
+
+// Occurrence counts over the sets [0, R) of instances that count their own
+// (a prefix of a shared RR store): zero them ...
+__global__ void __launch_bounds__(kSelThreads) bsel_cnt_clear(const SelDesc *d, uint32_t ni) {
+  for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
+    const SelDesc &D = d[i];
+    if (!D.active || !D.count_own) continue;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < D.n; x += gridDim.x * blockDim.x) D.cnt[x] = 0u;
+  }
+}
+
+// ... then count every member of every set j < R (one warp per set).
+__global__ void __launch_bounds__(kSelThreads) bsel_count(const SelDesc *d, uint32_t ni) {
+  const unsigned long long total = d[ni - 1].set_begin + d[ni - 1].R;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t g = warp; g < total; g += nwarps) {
+    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.set_begin; });
+    const SelDesc &D = d[i];
+    if (!D.count_own) continue;
+    const uint64_t j = g - D.set_begin;
+    const uint64_t b = D.rr_start[j];
+    const uint32_t len = D.rr_len[j];
+    for (uint32_t t = lane; t < len; t += 32) atomicAdd(&D.cnt[D.members[b + t]], 1u);
   }
 }
 
@@ -295,27 +322,82 @@ cudaError_t ensure_buf(T *&p, uint64_t &cap, uint64_t need) {
   return cudaSuccess;
 }
 
-struct ImmState {
-  ImmConst c;
-  int i = 1;             // lower-bound round (1-based)
-  int phase = 0;         // 0 lower-bound search, 1 final selection, 2 done
-  double LB = 1.0;
-  uint64_t theta = 0;
-  uint32_t rounds = 0;
-};
+// The fixed launch sequence of a batched selection: counts (for instances
+// that count a prefix), index build, max_k greedy rounds.
+cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uint32_t am_blocks,
+                              uint32_t fill_blocks, uint32_t max_k, uint32_t cnt_blocks, cudaStream_t s) {
+  bsel_clear<<<ni, kSelThreads, 0, s>>>(d, ni);
+  bsel_cnt_clear<<<dim3(cnt_blocks, std::min<uint32_t>(ni, 65535)), kSelThreads, 0, s>>>(d, ni);
+  bsel_count<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_tile_sums<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_tile_scan<<<ni, kSelThreads, 0, s>>>(d, ni);
+  bsel_apply<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_fill<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  for (uint32_t t = 0; t < max_k; ++t) {
+    bsel_argmax<<<am_blocks, kSelThreads, 0, s>>>(d, ni, t);
+    bsel_cover<<<ni * kCoverBlocks, kSelThreads, 0, s>>>(d, ni, t);
+  }
+  return cudaGetLastError();
+}
 
-// The batch's selection plumbing: descriptors, packed outputs, the graph.
-struct BatchSel {
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// IMM state machine (Alg. 2, then Alg. 1), advanced by the host.
+// ---------------------------------------------------------------------------
+void imm_init(ImmState &st, uint32_t n, const gim_imm_params &p) {
+  st = ImmState{};
+  st.c = imm_constants(n, p.k, p.eps, p.ell);
+  if (st.c.i_max < 1) {   // no lower-bound round: LB = 1
+    st.phase = 1;
+    st.theta = (uint64_t)std::ceil(st.c.lam2 / st.LB);
+  }
+}
+
+uint64_t imm_target(const ImmState &st, uint32_t n) {
+  if (st.phase == 0) {
+    const double x = (double)n / std::ldexp(1.0, st.i);
+    return (uint64_t)std::ceil(st.c.lam1 / x);
+  }
+  return st.theta;
+}
+
+void imm_advance(ImmState &st, uint32_t n, uint64_t R, uint64_t cov) {
+  if (st.phase == 1) {
+    st.phase = 2;
+    return;
+  }
+  st.rounds++;
+  const double x = (double)n / std::ldexp(1.0, st.i);
+  const double est = ((double)n * (double)cov) / (double)R;
+  bool stop = false;
+  if (est >= (1.0 + st.c.epsp) * x) {
+    st.LB = est / (1.0 + st.c.epsp);
+    stop = true;
+  } else if (++st.i > st.c.i_max) {
+    stop = true;
+  }
+  if (stop) {
+    st.phase = 1;
+    st.theta = (uint64_t)std::ceil(st.c.lam2 / st.LB);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MultiSelect: the greedy selection of many instances at once.
+// ---------------------------------------------------------------------------
+struct MultiSelect::Impl {
   std::vector<SelDesc> h;
   SelDesc *d = nullptr;
   uint32_t *seeds = nullptr;             // packed, sum of k
   uint32_t *gains = nullptr;
-  unsigned long long *covered = nullptr; // one per instance
+  unsigned long long *covered = nullptr; // one per slot
   std::vector<uint64_t> seed_off;
-  uint32_t scan_blocks = 0, am_blocks = 0, max_k = 0, fill_blocks = 0;
+  std::vector<uint32_t> k_cfg;
+  uint32_t ni = 0, scan_blocks = 0, am_blocks = 0, max_k = 0, fill_blocks = 0, cnt_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  ~BatchSel() {
+  ~Impl() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (d) cudaFree(d);
@@ -325,49 +407,20 @@ struct BatchSel {
   }
 };
 
-// Enqueues the whole batched selection (index build + max_k greedy rounds).
-cudaError_t enqueue_selection(BatchSel &B, uint32_t ni, cudaStream_t s) {
-  bsel_clear<<<ni, kSelThreads, 0, s>>>(B.d, ni);
-  bsel_tile_sums<<<B.scan_blocks, kSelThreads, 0, s>>>(B.d, ni);
-  bsel_tile_scan<<<ni, kSelThreads, 0, s>>>(B.d, ni);
-  bsel_apply<<<B.scan_blocks, kSelThreads, 0, s>>>(B.d, ni);
-  bsel_fill<<<B.fill_blocks, kSelThreads, 0, s>>>(B.d, ni);
-  for (uint32_t t = 0; t < B.max_k; ++t) {
-    bsel_argmax<<<B.am_blocks, kSelThreads, 0, s>>>(B.d, ni, t);
-    bsel_cover<<<ni * kCoverBlocks, kSelThreads, 0, s>>>(B.d, ni, t);
-  }
-  return cudaGetLastError();
-}
+MultiSelect::MultiSelect() : p(new Impl) {}
+MultiSelect::~MultiSelect() { delete p; }
 
-}  // namespace
-
-// Runs IMM on every context of the batch (see gim_batch_imm in gim.h).
-gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint32_t *const *seeds_out,
-                     gim_imm_result *results) {
-  gim_ctx *ctx = ctxs[0];
-  cudaStream_t s = ctx->stream;
-  const auto t0 = std::chrono::steady_clock::now();
-  std::vector<ImmState> S(ni);
-  for (uint32_t i = 0; i < ni; ++i) {
-    gim_ctx *c = ctxs[i];
-    c->R = c->Z = c->store_used = 0;
-    c->model = -1;
-    CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
-    S[i].c = imm_constants(c->g.n, params[i].k, params[i].eps, params[i].ell);
-    if (S[i].c.i_max < 1) {   // no lower-bound round: LB = 1
-      S[i].phase = 1;
-      S[i].theta = (uint64_t)std::ceil(S[i].c.lam2 / S[i].LB);
-    }
-  }
-  BatchSel B;
-  B.h.resize(ni);
-  B.seed_off.resize(ni + 1, 0);
-  uint32_t tiles = 0, am = 0;
-  for (uint32_t i = 0; i < ni; ++i) {
+gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k) {
+  Impl &B = *p;
+  B.ni = (uint32_t)n.size();
+  B.h.assign(B.ni, SelDesc{});
+  B.seed_off.assign(B.ni + 1, 0);
+  B.k_cfg = k;
+  uint32_t tiles = 0, am = 0, nmax = 0;
+  for (uint32_t i = 0; i < B.ni; ++i) {
     SelDesc &D = B.h[i];
-    D = SelDesc{};
-    D.n = ctxs[i]->g.n;
-    D.k = params[i].k;
+    D.n = n[i];
+    D.k = k[i];
     D.tile_begin = tiles;
     D.tiles = (D.n + kTile - 1) / kTile;
     tiles += D.tiles;
@@ -376,127 +429,157 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
     am += D.am_blocks;
     B.seed_off[i + 1] = B.seed_off[i] + D.k;
     B.max_k = std::max(B.max_k, D.k);
+    nmax = std::max(nmax, D.n);
   }
   B.scan_blocks = tiles;
   B.am_blocks = am;
   B.fill_blocks = (uint32_t)ctx->sm_count * 8;
-  CU(cudaMalloc(&B.d, ni * sizeof(SelDesc)));
-  CU(cudaMalloc(&B.seeds, B.seed_off[ni] * 4));
-  CU(cudaMalloc(&B.gains, B.seed_off[ni] * 4));
-  CU(cudaMalloc(&B.covered, ni * 8ull));
-  std::vector<unsigned long long> cov(ni);
-  std::vector<uint32_t> seeds(B.seed_off[ni]);
+  B.cnt_blocks = std::max<uint32_t>(1, std::min<uint32_t>((nmax + 4095) / 4096, 256));
+  CU(cudaMalloc(&B.d, std::max<uint32_t>(B.ni, 1) * sizeof(SelDesc)));
+  CU(cudaMalloc(&B.seeds, std::max<uint64_t>(B.seed_off[B.ni], 1) * 4));
+  CU(cudaMalloc(&B.gains, std::max<uint64_t>(B.seed_off[B.ni], 1) * 4));
+  CU(cudaMalloc(&B.covered, std::max<uint32_t>(B.ni, 1) * 8ull));
+  return GIM_OK;
+}
+
+uint64_t MultiSelect::seed_offset(uint32_t i) const { return p->seed_off[i]; }
+
+gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaStream_t s,
+                            std::vector<unsigned long long> &cov, std::vector<uint32_t> &seeds) {
+  Impl &B = *p;
+  unsigned long long total_sets = 0;
+  for (uint32_t i = 0; i < B.ni; ++i) {
+    SelDesc &D = B.h[i];
+    const SelInput &x = in[i];
+    D.active = x.active ? 1u : 0u;
+    D.k = x.k && x.k <= B.k_cfg[i] ? x.k : B.k_cfg[i];
+    D.set_begin = total_sets;
+    D.R = D.active ? x.R : 0;
+    D.count_own = 0;
+    if (!D.active) continue;
+    total_sets += x.R;
+    SelectBuffers &b = *x.buf;
+    if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || (!x.cnt && !b.cnt_own)) {
+      uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap, c3 = b.n_cap;
+      CU(ensure_buf(b.cnt_work, c0, (uint64_t)D.n + 4));
+      CU(ensure_buf(b.inv_off, c1, (uint64_t)D.n + 4));
+      CU(ensure_buf(b.cursor, c2, (uint64_t)D.n + 4));
+      if (!x.cnt) CU(ensure_buf(b.cnt_own, c3, (uint64_t)D.n + 4));
+      b.n_cap = std::min(c0, std::min(c1, c2));
+      if (!x.cnt) b.n_cap = std::min(b.n_cap, c3);
+    }
+    CU(ensure_buf(b.inv, b.z_cap, std::max<uint64_t>(x.Z, 1)));
+    CU(ensure_buf(b.covered, b.r_cap, std::max<uint64_t>(x.R, 1)));
+    if (b.k_cap < D.k || !b.best || !b.seeds || !b.gains) {   // the three k-sized buffers share k_cap
+      uint64_t k0 = b.k_cap, k1 = b.k_cap, k2 = b.k_cap;
+      CU(ensure_buf(b.best, k0, D.k));
+      CU(ensure_buf(b.seeds, k1, D.k));
+      CU(ensure_buf(b.gains, k2, D.k));
+      b.k_cap = std::min(k0, std::min(k1, k2));
+    }
+    CU(ensure_buf(b.scan_tmp, b.scan_cap, (uint64_t)D.tiles + 1));
+    D.members = x.members;
+    D.rr_start = x.rr_start;
+    D.rr_len = x.rr_len;
+    D.count_own = x.cnt ? 0u : 1u;
+    D.cnt = x.cnt ? const_cast<uint32_t *>(x.cnt) : b.cnt_own;
+    D.cnt_work = b.cnt_work;
+    D.inv_off = b.inv_off;
+    D.cursor = b.cursor;
+    D.inv = b.inv;
+    D.covered = b.covered;
+    D.best = b.best;
+    D.seeds = B.seeds + B.seed_off[i];
+    D.gains = B.gains + B.seed_off[i];
+    D.covered_total = B.covered + i;
+    D.tile_sum = b.scan_tmp;
+  }
+  CU(cudaMemcpyAsync(B.d, B.h.data(), B.ni * sizeof(SelDesc), cudaMemcpyHostToDevice, s));
+  if (!B.exec) {
+    // the launch sequence is fixed for these slots; the round's inputs live in B.d
+    CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ce =
+        enqueue_selection(B.d, B.ni, B.scan_blocks, B.am_blocks, B.fill_blocks, B.max_k, B.cnt_blocks, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
+    if (ce != cudaSuccess) return cuda_err(ctx, ce, "selection capture");
+    if (ee != cudaSuccess) return cuda_err(ctx, ee, "selection capture");
+    B.graph = g;
+    CU(cudaGraphInstantiate(&B.exec, B.graph, 0));
+  }
+  CU(cudaGraphLaunch(B.exec, s));
+  ctx->launches += 7 + 2ull * B.max_k;
+  cov.resize(B.ni);
+  seeds.resize(B.seed_off[B.ni]);
+  CU(cudaMemcpyAsync(cov.data(), B.covered, B.ni * 8ull, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(seeds.data(), B.seeds, B.seed_off[B.ni] * 4, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return GIM_OK;
+}
+
+// Runs IMM on every context of the batch (see gim_batch_imm in gim.h).
+gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint32_t *const *seeds_out,
+                     gim_imm_result *results) {
+  gim_ctx *ctx = ctxs[0];
+  cudaStream_t s = ctx->stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<ImmState> S(ni);
+  std::vector<uint32_t> ns(ni), ks(ni);
+  for (uint32_t i = 0; i < ni; ++i) {
+    gim_ctx *c = ctxs[i];
+    c->R = c->Z = c->store_used = 0;
+    c->model = -1;
+    CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
+    imm_init(S[i], c->g.n, params[i]);
+    ns[i] = c->g.n;
+    ks[i] = params[i].k;
+  }
+  MultiSelect ms;
+  gim_status st = ms.configure(ctx, ns, ks);
+  if (st != GIM_OK) return st;
+  std::vector<SelInput> in(ni);
+  std::vector<unsigned long long> cov;
+  std::vector<uint32_t> seeds;
   double t_sample = 0, t_select = 0;
   for (;;) {
     // 1. sampling up to every unfinished instance's target
     std::vector<SampleJobH> jobs;
     bool any = false;
     for (uint32_t i = 0; i < ni; ++i) {
-      ImmState &st = S[i];
-      if (st.phase == 2) continue;
+      if (S[i].phase == 2) continue;
       any = true;
       gim_ctx *c = ctxs[i];
-      uint64_t target;
-      if (st.phase == 0) {
-        const double x = (double)c->g.n / std::ldexp(1.0, st.i);
-        target = (uint64_t)std::ceil(st.c.lam1 / x);
-      } else {
-        target = st.theta;
-      }
+      const uint64_t target = imm_target(S[i], c->g.n);
       if (target >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "instance %u: theta above 2^32-2 RR sets", i);
       if (target > c->R) jobs.push_back(SampleJobH{c, (int)params[i].model, params[i].seed, target - c->R});
     }
     if (!any) break;
-    {
-      const auto ts = std::chrono::steady_clock::now();
-      gim_status st = sample_jobs(jobs, s);
-      if (st != GIM_OK) return st;
-      t_sample += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
-    }
+    auto ts = std::chrono::steady_clock::now();
+    if ((st = sample_jobs(jobs, s)) != GIM_OK) return st;
+    t_sample += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     // 2. selection over every unfinished instance's collection
-    const auto ts = std::chrono::steady_clock::now();
-    unsigned long long total_sets = 0;
+    ts = std::chrono::steady_clock::now();
     for (uint32_t i = 0; i < ni; ++i) {
-      SelDesc &D = B.h[i];
       gim_ctx *c = ctxs[i];
-      D.active = S[i].phase != 2;
-      D.set_begin = total_sets;
-      D.R = D.active ? c->R : 0;
-      if (!D.active) continue;
-      total_sets += c->R;
-      SelectBuffers &b = c->sel;
-      uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap;
-      CU(ensure_buf(b.cnt_work, c0, (uint64_t)D.n + 4));
-      CU(ensure_buf(b.inv_off, c1, (uint64_t)D.n + 4));
-      CU(ensure_buf(b.cursor, c2, (uint64_t)D.n + 4));
-      b.n_cap = std::min(c0, std::min(c1, c2));
-      CU(ensure_buf(b.inv, b.z_cap, std::max<uint64_t>(c->Z, 1)));
-      CU(ensure_buf(b.covered, b.r_cap, std::max<uint64_t>(c->R, 1)));
-      if (b.k_cap < D.k || !b.best || !b.seeds || !b.gains) {   // the three k-sized buffers share k_cap
-        uint64_t k0 = b.k_cap, k1 = b.k_cap, k2 = b.k_cap;
-        CU(ensure_buf(b.best, k0, D.k));
-        CU(ensure_buf(b.seeds, k1, D.k));
-        CU(ensure_buf(b.gains, k2, D.k));
-        b.k_cap = std::min(k0, std::min(k1, k2));
-      }
-      CU(ensure_buf(b.scan_tmp, b.scan_cap, (uint64_t)D.tiles + 1));
-      D.members = c->st.members;
-      D.rr_start = c->st.rr_start;
-      D.rr_len = c->st.rr_len;
-      D.cnt = c->st.cnt;
-      D.cnt_work = b.cnt_work;
-      D.inv_off = b.inv_off;
-      D.cursor = b.cursor;
-      D.inv = b.inv;
-      D.covered = b.covered;
-      D.best = b.best;
-      D.seeds = B.seeds + B.seed_off[i];
-      D.gains = B.gains + B.seed_off[i];
-      D.covered_total = B.covered + i;
-      D.tile_sum = b.scan_tmp;
+      SelInput &x = in[i];
+      x.active = S[i].phase != 2;
+      x.R = c->R;
+      x.Z = c->Z;
+      x.members = c->st.members;
+      x.rr_start = c->st.rr_start;
+      x.rr_len = c->st.rr_len;
+      x.cnt = c->st.cnt;
+      x.buf = &c->sel;
     }
-    CU(cudaMemcpyAsync(B.d, B.h.data(), ni * sizeof(SelDesc), cudaMemcpyHostToDevice, s));
-    if (!B.exec) {
-      // the launch sequence is fixed for the batch; round inputs live in B.d
-      CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      const cudaError_t ce = enqueue_selection(B, ni, s);
-      cudaGraph_t g = nullptr;
-      const cudaError_t ee = cudaStreamEndCapture(s, &g);
-      if (ce != cudaSuccess) return cuda_err(ctx, ce, "selection capture");
-      if (ee != cudaSuccess) return cuda_err(ctx, ee, "selection capture");
-      B.graph = g;
-      CU(cudaGraphInstantiate(&B.exec, B.graph, 0));
-    }
-    CU(cudaGraphLaunch(B.exec, s));
-    ctx->launches += 5 + 2ull * B.max_k;
-    CU(cudaMemcpyAsync(cov.data(), B.covered, ni * 8ull, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(seeds.data(), B.seeds, B.seed_off[ni] * 4, cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
+    if ((st = ms.run(ctx, in, s, cov, seeds)) != GIM_OK) return st;
     t_select += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
-    // 3. advance every instance's state machine (Alg. 2, then Alg. 1)
+    // 3. advance every instance's state machine
     for (uint32_t i = 0; i < ni; ++i) {
-      ImmState &st = S[i];
-      if (st.phase == 2) continue;
-      gim_ctx *c = ctxs[i];
-      if (st.phase == 1) {
-        st.phase = 2;
-        std::copy(seeds.begin() + B.seed_off[i], seeds.begin() + B.seed_off[i + 1], seeds_out[i]);
-        continue;
-      }
-      st.rounds++;
-      const double x = (double)c->g.n / std::ldexp(1.0, st.i);
-      const double est = ((double)c->g.n * (double)cov[i]) / (double)c->R;
-      bool stop = false;
-      if (est >= (1.0 + st.c.epsp) * x) {
-        st.LB = est / (1.0 + st.c.epsp);
-        stop = true;
-      } else if (++st.i > st.c.i_max) {
-        stop = true;
-      }
-      if (stop) {
-        st.phase = 1;
-        st.theta = (uint64_t)std::ceil(st.c.lam2 / st.LB);
-      }
+      if (S[i].phase == 2) continue;
+      const bool final_round = S[i].phase == 1;
+      imm_advance(S[i], ctxs[i]->g.n, ctxs[i]->R, cov[i]);
+      if (final_round)
+        std::copy(seeds.begin() + ms.seed_offset(i), seeds.begin() + ms.seed_offset(i + 1), seeds_out[i]);
     }
   }
   for (uint32_t i = 0; i < ni; ++i) {

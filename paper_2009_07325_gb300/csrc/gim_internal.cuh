@@ -177,6 +177,7 @@ struct SelectBuffers {
   uint32_t *gains = nullptr;     // k
   unsigned long long *covered_total = nullptr;
   uint64_t *scan_tmp = nullptr;  // block partial sums
+  uint32_t *cnt_own = nullptr;   // n: counts over a prefix of a shared store (serving)
   uint64_t n_cap = 0, z_cap = 0, r_cap = 0, k_cap = 0, scan_cap = 0;
 };
 
@@ -228,6 +229,48 @@ void shared_release(int device);
 DeviceShared &device_shared(int device);
 gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s);
 
+// IMM state machine (batch.cu): the lower-bound search of Alg. 2, then the
+// final sampling and selection, advanced by the host one round at a time.
+struct ImmState {
+  ImmConst c;
+  int i = 1;             // lower-bound round (1-based)
+  int phase = 0;         // 0 lower-bound search, 1 final selection, 2 done
+  double LB = 1.0;
+  uint64_t theta = 0;
+  uint32_t rounds = 0;
+};
+void imm_init(ImmState &st, uint32_t n, const gim_imm_params &p);
+uint64_t imm_target(const ImmState &st, uint32_t n);                  // RR sets the next selection needs
+void imm_advance(ImmState &st, uint32_t n, uint64_t R, uint64_t cov);  // after a selection over R sets
+
+// One instance of a batched selection round.
+struct SelInput {
+  bool active = false;
+  uint64_t R = 0, Z = 0;                 // sets [0, R) with Z members in all (Z bounds the index)
+  const uint32_t *members = nullptr;
+  const uint64_t *rr_start = nullptr;
+  const uint32_t *rr_len = nullptr;
+  const uint32_t *cnt = nullptr;         // occurrence counts over [0, R); null: counted here
+  SelectBuffers *buf = nullptr;          // the instance's selection buffers (grown on demand)
+  uint32_t k = 0;                        // rounds this time (<= the configured k); 0: the configured k
+};
+
+// Greedy selection of a fixed set of slots (n, k fixed), one CUDA graph per
+// configuration replayed for every round.
+class MultiSelect {
+ public:
+  MultiSelect();
+  ~MultiSelect();
+  gim_status configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k);
+  gim_status run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaStream_t s, std::vector<unsigned long long> &cov,
+                 std::vector<uint32_t> &seeds);
+  uint64_t seed_offset(uint32_t i) const;
+
+ private:
+  struct Impl;
+  Impl *p;
+};
+
 // tune.cu
 gim_status autotune(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *params, uint64_t sample_sets,
                     uint64_t *budget_out, int *measured_out);
@@ -250,6 +293,7 @@ struct gim_ctx {
   uint64_t launches = 0;
 
   bool has_graph = false;
+  bool owns_graph = true;         // false for a server pool that shares another context's graph
   int lt_ok = 0;
   uint32_t max_indeg = 0;         // of the loaded graph (degree profile of the autotuner)
   gim::DevGraph g;
