@@ -28,13 +28,14 @@ namespace {
 constexpr int kSelThreads = 256;
 constexpr uint32_t kTile = 4096;        // vertices per scan tile (256 threads x 16)
 constexpr uint32_t kTileItems = kTile / kSelThreads;
-constexpr uint32_t kCoverBlocks = 8;    // cover blocks per instance
 
 // One instance of a batched selection. Block ranges are fixed for the batch.
 struct SelDesc {
   uint32_t n, k, active, count_own;       // count_own: cnt is computed here from sets [0, R)
   unsigned long long R;
   unsigned long long set_begin;           // prefix of R over the batch (fill kernel)
+  unsigned long long count_from;          // count_own: sets [0, count_from) are already in cnt
+  unsigned long long cnt_begin;           // prefix of the sets counted this round (count kernel)
   const uint32_t *members;
   const uint64_t *rr_start;
   const uint32_t *rr_len;
@@ -51,6 +52,7 @@ struct SelDesc {
   uint64_t *tile_sum;                     // tiles
   uint32_t tile_begin, tiles;             // scan blocks of this instance
   uint32_t am_begin, am_blocks;           // argmax blocks
+  uint32_t cv_begin, cv_blocks;           // cover blocks
 };
 
 // Instance of block b: the last i with begin(i) <= b.
@@ -120,22 +122,25 @@ __global__ void __launch_bounds__(kSelThreads) bsel_clear(const SelDesc *d, uint
 __global__ void __launch_bounds__(kSelThreads) bsel_cnt_clear(const SelDesc *d, uint32_t ni) {
   for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
     const SelDesc &D = d[i];
-    if (!D.active || !D.count_own) continue;
+    if (!D.active || !D.count_own || D.count_from != 0) continue;
     for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < D.n; x += gridDim.x * blockDim.x) D.cnt[x] = 0u;
   }
 }
 
-// ... then count every member of every set j < R (one warp per set).
+// ... then count every member of every set j in [count_from, R) (one warp per set).
+__device__ __forceinline__ unsigned long long counted(const SelDesc &x) {
+  return x.active && x.count_own ? x.R - x.count_from : 0ull;
+}
+
 __global__ void __launch_bounds__(kSelThreads) bsel_count(const SelDesc *d, uint32_t ni) {
-  const unsigned long long total = d[ni - 1].set_begin + d[ni - 1].R;
+  const unsigned long long total = d[ni - 1].cnt_begin + counted(d[ni - 1]);
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t g = warp; g < total; g += nwarps) {
-    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.set_begin; });
+    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.cnt_begin; });
     const SelDesc &D = d[i];
-    if (!D.count_own) continue;
-    const uint64_t j = g - D.set_begin;
+    const uint64_t j = D.count_from + (g - D.cnt_begin);
     const uint64_t b = D.rr_start[j];
     const uint32_t len = D.rr_len[j];
     for (uint32_t t = lane; t < len; t += 32) atomicAdd(&D.cnt[D.members[b + t]], 1u);
@@ -258,10 +263,9 @@ __global__ void __launch_bounds__(kSelThreads) bsel_argmax(const SelDesc *d, uin
 // Round t: record the chosen seed, mark it selected, cover its uncovered sets.
 __global__ void __launch_bounds__(kSelThreads) bsel_cover(const SelDesc *d, uint32_t ni, uint32_t t) {
   __shared__ unsigned long long part[kSelThreads / 32];
-  const uint32_t i = blockIdx.x / kCoverBlocks;
-  const uint32_t lb = blockIdx.x % kCoverBlocks;
-  if (i >= ni) return;
+  const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.cv_begin; });
   const SelDesc &D = d[i];
+  const uint32_t lb = blockIdx.x - D.cv_begin;
   if (!D.active || t >= D.k) return;
   const unsigned long long key = D.best[t];
   const uint32_t u = ~(uint32_t)(key & 0xFFFFFFFFull);
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_cover(const SelDesc *d, uint
   }
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (lb * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (kCoverBlocks * blockDim.x) >> 5;
+  const uint32_t nwarps = (D.cv_blocks * blockDim.x) >> 5;
   const uint64_t i0 = D.inv_off[u], i1 = D.inv_off[u + 1];
   unsigned long long newly = 0;
   for (uint64_t p = i0 + warp; p < i1; p += nwarps) {
@@ -325,7 +329,8 @@ cudaError_t ensure_buf(T *&p, uint64_t &cap, uint64_t need) {
 // The fixed launch sequence of a batched selection: counts (for instances
 // that count a prefix), index build, max_k greedy rounds.
 cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uint32_t am_blocks,
-                              uint32_t fill_blocks, uint32_t max_k, uint32_t cnt_blocks, cudaStream_t s) {
+                              uint32_t cv_blocks, uint32_t fill_blocks, uint32_t max_k, uint32_t cnt_blocks,
+                              cudaStream_t s) {
   bsel_clear<<<ni, kSelThreads, 0, s>>>(d, ni);
   bsel_cnt_clear<<<dim3(cnt_blocks, std::min<uint32_t>(ni, 65535)), kSelThreads, 0, s>>>(d, ni);
   bsel_count<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
@@ -335,7 +340,7 @@ cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uin
   bsel_fill<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
   for (uint32_t t = 0; t < max_k; ++t) {
     bsel_argmax<<<am_blocks, kSelThreads, 0, s>>>(d, ni, t);
-    bsel_cover<<<ni * kCoverBlocks, kSelThreads, 0, s>>>(d, ni, t);
+    bsel_cover<<<cv_blocks, kSelThreads, 0, s>>>(d, ni, t);
   }
   return cudaGetLastError();
 }
@@ -394,7 +399,7 @@ struct MultiSelect::Impl {
   unsigned long long *covered = nullptr; // one per slot
   std::vector<uint64_t> seed_off;
   std::vector<uint32_t> k_cfg;
-  uint32_t ni = 0, scan_blocks = 0, am_blocks = 0, max_k = 0, fill_blocks = 0, cnt_blocks = 0;
+  uint32_t ni = 0, scan_blocks = 0, am_blocks = 0, cv_blocks = 0, max_k = 0, fill_blocks = 0, cnt_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~Impl() {
@@ -416,7 +421,7 @@ gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, 
   B.h.assign(B.ni, SelDesc{});
   B.seed_off.assign(B.ni + 1, 0);
   B.k_cfg = k;
-  uint32_t tiles = 0, am = 0, nmax = 0;
+  uint32_t tiles = 0, am = 0, cv = 0, nmax = 0;
   for (uint32_t i = 0; i < B.ni; ++i) {
     SelDesc &D = B.h[i];
     D.n = n[i];
@@ -427,12 +432,17 @@ gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, 
     D.am_begin = am;
     D.am_blocks = std::max<uint32_t>(1, std::min<uint32_t>((D.n + 4095) / 4096, 64));
     am += D.am_blocks;
+    // cover parallelism grows with the graph: a hub seed covers a large share of the sets
+    D.cv_begin = cv;
+    D.cv_blocks = std::max<uint32_t>(8, std::min<uint32_t>((D.n + 65535) / 65536, 256));
+    cv += D.cv_blocks;
     B.seed_off[i + 1] = B.seed_off[i] + D.k;
     B.max_k = std::max(B.max_k, D.k);
     nmax = std::max(nmax, D.n);
   }
   B.scan_blocks = tiles;
   B.am_blocks = am;
+  B.cv_blocks = cv;
   B.fill_blocks = (uint32_t)ctx->sm_count * 8;
   B.cnt_blocks = std::max<uint32_t>(1, std::min<uint32_t>((nmax + 4095) / 4096, 256));
   CU(cudaMalloc(&B.d, std::max<uint32_t>(B.ni, 1) * sizeof(SelDesc)));
@@ -447,18 +457,21 @@ uint64_t MultiSelect::seed_offset(uint32_t i) const { return p->seed_off[i]; }
 gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaStream_t s,
                             std::vector<unsigned long long> &cov, std::vector<uint32_t> &seeds) {
   Impl &B = *p;
-  unsigned long long total_sets = 0;
+  unsigned long long total_sets = 0, total_counted = 0;
   for (uint32_t i = 0; i < B.ni; ++i) {
     SelDesc &D = B.h[i];
     const SelInput &x = in[i];
     D.active = x.active ? 1u : 0u;
     D.k = x.k && x.k <= B.k_cfg[i] ? x.k : B.k_cfg[i];
     D.set_begin = total_sets;
+    D.cnt_begin = total_counted;
     D.R = D.active ? x.R : 0;
     D.count_own = 0;
+    D.count_from = 0;
     if (!D.active) continue;
     total_sets += x.R;
     SelectBuffers &b = *x.buf;
+    const uint32_t *own_before = b.cnt_own;
     if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || (!x.cnt && !b.cnt_own)) {
       uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap, c3 = b.n_cap;
       CU(ensure_buf(b.cnt_work, c0, (uint64_t)D.n + 4));
@@ -483,6 +496,12 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     D.rr_len = x.rr_len;
     D.count_own = x.cnt ? 0u : 1u;
     D.cnt = x.cnt ? const_cast<uint32_t *>(x.cnt) : b.cnt_own;
+    if (!x.cnt) {
+      // counts carried over from the slot's previous round survive only in the same buffer
+      const bool keep = b.cnt_own == own_before && x.count_from <= x.R;
+      D.count_from = keep ? x.count_from : 0;
+      total_counted += x.R - D.count_from;
+    }
     D.cnt_work = b.cnt_work;
     D.inv_off = b.inv_off;
     D.cursor = b.cursor;
@@ -499,7 +518,8 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     // the launch sequence is fixed for these slots; the round's inputs live in B.d
     CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const cudaError_t ce =
-        enqueue_selection(B.d, B.ni, B.scan_blocks, B.am_blocks, B.fill_blocks, B.max_k, B.cnt_blocks, s);
+        enqueue_selection(B.d, B.ni, B.scan_blocks, B.am_blocks, B.cv_blocks, B.fill_blocks, B.max_k, B.cnt_blocks,
+                          s);
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s, &g);
     if (ce != cudaSuccess) return cuda_err(ctx, ce, "selection capture");

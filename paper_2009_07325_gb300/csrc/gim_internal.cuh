@@ -250,7 +250,8 @@ struct SelInput {
   const uint32_t *members = nullptr;
   const uint64_t *rr_start = nullptr;
   const uint32_t *rr_len = nullptr;
-  const uint32_t *cnt = nullptr;         // occurrence counts over [0, R); null: counted here
+  const uint32_t *cnt = nullptr;         // occurrence counts over [0, R); null: counted into buf->cnt_own
+  uint64_t count_from = 0;               // cnt == null: buf->cnt_own already counts sets [0, count_from)
   SelectBuffers *buf = nullptr;          // the instance's selection buffers (grown on demand)
   uint32_t k = 0;                        // rounds this time (<= the configured k); 0: the configured k
 };

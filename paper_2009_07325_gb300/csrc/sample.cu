@@ -23,8 +23,8 @@
 //   epoch, so it is never cleared. A set that outgrows the queue or scans
 //   more than its edge budget is abandoned and deferred.
 // IC, large-set pass: one 512-thread block per deferred set, with an n-bit
-//   visited bitmap and an n-entry queue. Each batch of up to 64 frontier
-//   vertices is cut into chunks of at most 2048 in-edges that the block's
+//   visited bitmap and an n-entry queue. Each batch of up to 256 frontier
+//   vertices is cut into chunks of at most 1024 in-edges that the block's
 //   warps take from a shared counter, so the heavy tail of huge RR sets is
 //   spread over 16 warps. Only __syncthreads barriers are used.
 // LT: the reverse walk of Sec. III-G, one warp per walk: one draw per step,

@@ -43,6 +43,7 @@ struct Query {
   gim_ctx *pool = nullptr;
   int slot = -1;
   uint64_t Rq = 0;                 // the prefix of the pool this query's run has reached
+  uint64_t counted = 0;            // sets [0, counted) are already in the slot's occurrence counts
   uint64_t projected = 0;          // admission bytes
   std::vector<uint32_t> seeds;
   gim_imm_result res{};
@@ -181,7 +182,8 @@ gim_status round_once(gim_server *S, std::vector<Query *> &active) {
     x.members = q->pool->st.members;
     x.rr_start = q->pool->st.rr_start;
     x.rr_len = q->pool->st.rr_len;
-    x.cnt = nullptr;           // counted over the prefix
+    x.cnt = nullptr;           // counted over the prefix, incrementally across the query's rounds
+    x.count_from = q->counted;
     x.k = q->p.k;
     x.buf = &S->slot_buf[q->slot];
   }
@@ -193,6 +195,7 @@ gim_status round_once(gim_server *S, std::vector<Query *> &active) {
   S->select_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
   // 3. advance the state machines
   for (Query *q : active) {
+    q->counted = q->Rq;
     const bool final_round = q->st.phase == 1;
     imm_advance(q->st, n, q->Rq, cov[q->slot]);
     if (final_round) {
