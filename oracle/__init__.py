@@ -90,6 +90,9 @@ def _lib_():
             L.orc_imm.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_uint64, ctypes.c_int, u32p, u64p, f64p, f64p]
             L.orc_imm.restype = ctypes.c_int
+            L.orc_imm_replay.argtypes = [vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, u32p, u64p, f64p,
+                                         f64p]
+            L.orc_imm_replay.restype = ctypes.c_int
             L.orc_max_threads.argtypes = []
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -182,6 +185,27 @@ class Oracle:
         mem = np.array([x for s in sets for x in s] or [0], np.uint32)
         if self.L.orc_load_collection(self.h, len(sets), off, mem) != 0:
             raise ValueError("bad collection")
+
+    def load_csr(self, offsets, members) -> None:
+        """Replace R with the collection given as CSR arrays (offsets: |R|+1, members)."""
+        off = np.ascontiguousarray(offsets, np.uint64)
+        mem = np.ascontiguousarray(members, np.uint32) if len(members) else np.zeros(1, np.uint32)
+        if self.L.orc_load_collection(self.h, len(off) - 1, off, mem) != 0:
+            raise ValueError("bad collection")
+
+    def imm_replay(self, k: int, eps: float, ell: float):
+        """IMM (Alg. 2 then Alg. 1) with every sampling step served by a prefix of
+        the loaded collection; |R| is left at the prefix IMM used."""
+        seeds = np.zeros(k, np.uint32)
+        theta = np.zeros(1, np.uint64)
+        lb = np.zeros(1, np.float64)
+        trace = np.zeros(4 * 64, np.float64)
+        rc = self.L.orc_imm_replay(self.h, k, eps, ell, seeds, theta, lb, trace)
+        if rc < 0:
+            raise RuntimeError(f"oracle imm replay failed ({rc})")
+        tr = trace[: 4 * min(rc, 64)].reshape(-1, 4)
+        rounds = [dict(x=r[0], theta_i=int(r[1]), covered=int(r[2]), rr_count=int(r[3])) for r in tr]
+        return dict(seeds=seeds, theta=int(theta[0]), lb=float(lb[0]), rounds=rounds, rr_count=self.rr_count)
 
     def reset(self) -> None:
         self.L.orc_reset(self.h)

@@ -452,10 +452,20 @@ void orc_imm_constants(uint32_t n, uint32_t k, double eps, double ell, double ou
  * 64 rounds): {x, theta_i, covered, |R|}. Returns the number of lower-bound
  * rounds, or a negative error.
  */
-int orc_imm(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed, int threads,
-            uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
-  if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
-  if (g->count != 0) return -1;
+/*
+ * "Sample until |R| >= target": draw fresh sets (avail == 0), or, when the
+ * collection was preloaded with avail sets, expose its first target sets.
+ */
+static int grow_to(orc *g, int model, uint64_t seed, int threads, uint64_t avail, uint64_t target) {
+  if (g->count >= target) return 0;
+  if (!avail) return orc_sample(g, model, seed, target - g->count, threads);
+  if (target > avail) return -4;
+  g->count = target;
+  return 0;
+}
+
+static int imm_core(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed, int threads,
+                    uint64_t avail, uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
   double c[5];
   orc_imm_constants(g->n, k, eps, ell, c);
   const double epsp = c[1], lam_prime = c[2], lam_star = c[3];
@@ -465,10 +475,8 @@ int orc_imm(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed
   for (int i = 1; i <= i_max; ++i) {
     const double x = (double)g->n / ldexp(1.0, i);
     const uint64_t theta_i = (uint64_t)ceil(lam_prime / x);
-    if (g->count < theta_i) {
-      int rc = orc_sample(g, model, seed, theta_i - g->count, threads);
-      if (rc) return rc;
-    }
+    int rc = grow_to(g, model, seed, threads, avail, theta_i);
+    if (rc) return rc;
     int64_t cov = orc_greedy(g, k, seeds, NULL);
     if (cov < 0) return -2;
     if (trace && rounds < 64) {
@@ -485,14 +493,38 @@ int orc_imm(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed
     }
   }
   const uint64_t theta = (uint64_t)ceil(lam_star / LB);
-  if (g->count < theta) {
-    int rc = orc_sample(g, model, seed, theta - g->count, threads);
-    if (rc) return rc;
-  }
+  int rc = grow_to(g, model, seed, threads, avail, theta);
+  if (rc) return rc;
   if (orc_greedy(g, k, seeds, NULL) < 0) return -2;
   if (theta_out) *theta_out = theta;
   if (lb_out) *lb_out = LB;
   return rounds;
+}
+
+int orc_imm(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed, int threads,
+            uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
+  if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
+  if (g->count != 0) return -1;
+  return imm_core(g, model, k, eps, ell, seed, threads, 0, seeds, theta_out, lb_out, trace);
+}
+
+/*
+ * IMM over a preloaded collection: the same steps as orc_imm, with every
+ * "sample until |R| >= t" served by the first t sets of the collection that
+ * orc_load_collection installed (which must hold RR sets 0, 1, ... of one
+ * (model, seed) in rr_id order). Afterwards |R| is the prefix IMM used.
+ * Returns the lower-bound rounds, -4 if the collection is too short for the
+ * theta it needs, or another negative error.
+ */
+int orc_imm_replay(orc *g, uint32_t k, double eps, double ell, uint32_t *seeds, uint64_t *theta_out,
+                   double *lb_out, double *trace) {
+  if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
+  const uint64_t avail = g->count;
+  if (!avail) return -1;
+  g->count = 0;
+  const int rc = imm_core(g, 0, k, eps, ell, 0, 1, avail, seeds, theta_out, lb_out, trace);
+  if (rc < 0) g->count = avail;
+  return rc;
 }
 
 int orc_max_threads(void) {

@@ -116,3 +116,27 @@ def test_imm_rejects_bad_arguments(oracle_mod, inputs_mod):
     for k, eps, ell in [(0, 0.5, 1.0), (51, 0.5, 1.0), (5, 0.0, 1.0), (5, 1.0, 1.0), (5, 0.5, 0.0)]:
         with pytest.raises(RuntimeError):
             o.imm(oracle_mod.IC, k, eps, ell, 1)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_imm_replay_equals_fresh_imm(oracle_mod, inputs_mod, model):
+    """IMM over a preloaded collection of RR sets 0, 1, ... (what the full-size
+    GPU checks use) takes the same steps as IMM that samples them itself."""
+    g = inputs_mod.wc_weights(inputs_mod.er(2000, 20000, 1))
+    mdl = oracle_mod.IC if model == "ic" else oracle_mod.LT
+    fresh = oracle_mod.Oracle(g).imm(mdl, 10, 0.5, 1.0, 7)
+    pool = oracle_mod.Oracle(g)
+    pool.sample(mdl, 7, fresh["rr_count"] + 5000, 1)
+    off, mem = pool.export()
+    rep = oracle_mod.Oracle(g)
+    rep.load_csr(off, mem)
+    r = rep.imm_replay(10, 0.5, 1.0)
+    assert r["seeds"].tolist() == fresh["seeds"].tolist()
+    assert (r["theta"], r["lb"], r["rr_count"]) == (fresh["theta"], fresh["lb"], fresh["rr_count"])
+    assert r["rounds"] == fresh["rounds"]
+    _check_trace(oracle_mod, g, r, 10, 0.5, 1.0)
+    # a collection shorter than the theta IMM needs is an error, not a silent answer
+    short = oracle_mod.Oracle(g)
+    short.load_csr(off[: fresh["rr_count"]], mem[: int(off[fresh["rr_count"] - 1])])
+    with pytest.raises(RuntimeError):
+        short.imm_replay(10, 0.5, 1.0)
