@@ -413,6 +413,19 @@ def roofline(kname, coins, alg_bytes, members, kern_s, n_launch, philox_calls_pe
     return base
 
 
+def select_roofline(sel: dict, hbm_peak: float, peak_kind: str):
+    """Greedy selection (index build + k rounds) against HBM: its algorithmic bytes
+    (counted by the library per selection) over the device time of its kernels."""
+    secs = sel["kernel_ms"] / 1e3
+    if secs <= 0 or sel["calls"] == 0:
+        return None
+    gbs = sel["bytes"] / secs / 1e9
+    return {"kernels": "bsel_* + greedy_kernel", "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+            "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": peak_kind,
+            "ms_per_selection": sel["kernel_ms"] / sel["calls"], "selections": sel["calls"],
+            "bytes_per_selection": sel["bytes"] / sel["calls"], "traffic": None}
+
+
 def cpu_baseline(graph, budget_s: float = 12.0):
     """The oracle, as it stands, on a bounded sample of the workload on all host cores."""
     import oracle as O
@@ -476,7 +489,12 @@ def run_ours(args):
 
     mdl = model_id()
     from paper_2009_07325_gb300 import binding
-    budget, _ = binding.autotune([ctx], [(mdl, k, eps, ell, seed)], 20000)   # schedule for this profile
+    if args.group_budget:   # a fixed schedule (profiler runs: timings under a profiler mislead the tuner)
+        ctx.set_option(binding.GIM_OPT_GROUP_BUDGET, args.group_budget)
+        budget, tuned_by = args.group_budget, "--group-budget"
+    else:
+        budget, _ = binding.autotune([ctx], [(mdl, k, eps, ell, seed)], 20000)   # schedule for this profile
+        tuned_by = "gim_autotune"
     for _ in range(args.warmup):
         ctx.imm(mdl, k, eps, ell, seed)
 
@@ -509,6 +527,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     tk = ctx.timings()
+    sel = ctx.selection_stats()
     launches = ctx.launch_count() - launches0
     philox_calls_per_s = ctx.philox_rate()       # measured ALU ceiling (after the timed region)
     local_s = sum(step_ms) / 1e3
@@ -545,13 +564,14 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas{world}", l2="flushed between steps (512 MiB write)"),
             "imm_s": secs / args.steps, "theta": thetas[-1], "rr_sets_per_step": rr_sets / args.steps,
-            "tuning": {"group_budget": budget, "by": "gim_autotune"},
+            "tuning": {"group_budget": budget, "by": tuned_by},
             "sample_ms_per_step": sample_ms / args.steps, "select_ms_per_step": select_ms / args.steps,
             "e2e": {"value": e2e_u / e2e_s, "unit": "RR-sets/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3))},
             "gpu_launches": launches,
             "roofline": roofline(kname, coins, alg_bytes, members_total, kern_s, n_launch, philox_calls_per_s,
                                  hbm_peak, peak_kind, traffic, tk["large_launches"]),
+            "select_roofline": select_roofline(sel, hbm_peak, peak_kind),
             "clocks": clk.summary(),
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -575,6 +595,9 @@ def run_case(args):
     g = I.uniform_weights(base, 0.01) if args.case == "sample-ic-p001" else I.wc_weights(base)
     model = GIM_LT if args.case == "sample-lt" else GIM_IC
     ctx = Context(0)
+    if args.large_bytes:
+        from paper_2009_07325_gb300 import binding
+        ctx.set_option(binding.GIM_OPT_LARGE_PASS_BYTES, int(args.large_bytes))
     ctx.load(g)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -603,6 +626,10 @@ def main():
     ap.add_argument("--case", default=None, choices=["sample-ic", "sample-lt", "sample-ic-p001", "select"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--count", type=int, default=20000, help="RR sets for --case")
+    ap.add_argument("--group-budget", type=int, default=0,
+                    help="fix GIM_OPT_GROUP_BUDGET instead of autotuning (for profiler runs)")
+    ap.add_argument("--large-bytes", type=float, default=0,
+                    help="--case: device bytes for the block-per-set pass scratch (keeps profiler captures small)")
     ap.add_argument("--workload", default="imm-ic-wc-rmat22", choices=sorted(WORKLOADS),
                     help="IMM workload (default: the headline)")
     args = ap.parse_args()

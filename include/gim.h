@@ -266,7 +266,13 @@ void gim_server_stop(gim_server *srv);
 typedef enum {
   /* In-edge groups (4 in-edges each) one RR set may scan in the warp-per-set
      IC pass before it is handed to the block-per-set pass. Default 16384. */
-  GIM_OPT_GROUP_BUDGET = 0
+  GIM_OPT_GROUP_BUDGET = 0,
+  /* Device bytes for the scratch of the block-per-set pass (an n-bit visited
+     bitmap and an n-entry queue per heavy RR set in flight; per device,
+     shared by its contexts). Heavy sets in flight = min(bytes / (n/8 + 4n),
+     8 x SM count), at least 1. Default 16 GiB; lower it to leave room for
+     other work on the GPU. */
+  GIM_OPT_LARGE_PASS_BYTES = 1
 } gim_option;
 
 /* Sets a tuning knob. Errors: GIM_ERR_ARG (unknown option or value 0). */
@@ -277,7 +283,7 @@ gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value);
 
 /*
  * Autotuner: picks GIM_OPT_GROUP_BUDGET - how long one warp keeps an RR set
- * before a 512-thread block takes it over, i.e. warps per RR set for heavy
+ * before a 256-thread block takes it over, i.e. warps per RR set for heavy
  * sets - for a workload, by timing the sampling of `sample_sets` RR sets
  * per instance under each candidate (4096 .. 2^30 groups) exactly as
  * gim_batch_imm (n_inst > 1) or gim_imm (n_inst = 1) would launch it. The
@@ -319,8 +325,23 @@ gim_status gim_coverage_export(gim_ctx *ctx, uint32_t *cnt_out);
  */
 gim_status gim_last_timings(gim_ctx *ctx, double out[8]);
 
-/* Zeroes the accumulated kernel counters of gim_last_timings (out[4..7]). */
+/* Zeroes the accumulated kernel counters of gim_last_timings (out[4..7])
+   and of gim_selection_stats. */
 gim_status gim_reset_timings(gim_ctx *ctx);
+
+/*
+ * Greedy selections (the maximum-coverage step of Alg. 1, Sec. III-H) run
+ * with this context since gim_reset_timings, accumulated: out[0] device time
+ * of the selection kernels in ms (CUDA events on the stream around the index
+ * build and the k rounds), out[1] their algorithmic bytes (8 per store
+ * member for reading the store and writing the index, 4 per vertex for the
+ * count scan, per round 4 per vertex for the argmax and 4 per word of the
+ * seed's list or bitmap row, 12 per member of each newly covered set, and
+ * the covered bitmap), out[2] selections, out[3] members of newly covered
+ * sets. out must hold 4 doubles. Batched and served selections are
+ * accounted to the first context of the batch or the server's graph context.
+ */
+gim_status gim_selection_stats(gim_ctx *ctx, double out[4]);
 
 /*
  * Diagnostic: the device's throughput of Philox4x32-10 blocks (the coin

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgim.so")
 
 GIM_IC, GIM_LT = 0, 1
 GIM_OPT_GROUP_BUDGET = 0
+GIM_OPT_LARGE_PASS_BYTES = 1
 STATUS = {0: "GIM_OK", 1: "GIM_ERR_ARG", 2: "GIM_ERR_OOM", 3: "GIM_ERR_CUDA", 4: "GIM_ERR_TIMEOUT",
           5: "GIM_ERR_STATE"}
 
@@ -69,6 +70,7 @@ SIGNATURES = {
     "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
     "gim_last_timings": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_reset_timings": (ctypes.c_int, [_vp]),
+    "gim_selection_stats": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_diag_philox_rate": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_launch_count": (ctypes.c_int, [_vp, _c_u64p]),
     "gim_last_error_string": (ctypes.c_char_p, [_vp]),
@@ -210,6 +212,12 @@ class Context:
 
     def reset_timings(self):
         self._check(self.L.gim_reset_timings(self.h), "gim_reset_timings")
+
+    def selection_stats(self) -> dict:
+        """Selections since reset_timings: device ms, algorithmic bytes, calls, covered-set members."""
+        out = np.zeros(4, np.float64)
+        self._check(self.L.gim_selection_stats(self.h, _p(out, _c_f64p)), "gim_selection_stats")
+        return dict(kernel_ms=out[0], bytes=out[1], calls=int(out[2]), covered_members=out[3])
 
     def philox_rate(self) -> float:
         """Measured Philox4x32-10 calls per second of this device (ALU ceiling of the coins)."""

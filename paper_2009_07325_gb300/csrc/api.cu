@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "gim_internal.cuh"
@@ -31,6 +32,7 @@ void free_graph(DevGraph &g) {
   dfree(g.src);
   dfree(g.thr);
   dfree(g.rthr);
+  dfree(g.rw);
   dfree(g.cum);
   g = DevGraph{};
 }
@@ -47,6 +49,9 @@ void free_select(SelectBuffers &b) {
   dfree(b.covered_total);
   dfree(b.scan_tmp);
   dfree(b.cnt_own);
+  dfree(b.hslot);
+  dfree(b.hbits);
+  dfree(b.hmeta);
   b = SelectBuffers{};
 }
 
@@ -70,14 +75,35 @@ gim_status check_ctx(gim_ctx *ctx) {
 
 gim_status do_select(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *covered_out, uint32_t *gains_out) {
   if (ctx->R >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "more than 2^32-2 RR sets");
-  CU(run_select(ctx->g, ctx->st, ctx->R, ctx->Z, k, ctx->sel, ctx->sm_count, ctx->stream, &ctx->launches));
-  CU(cudaMemcpyAsync(seeds_out, ctx->sel.seeds, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  if (gains_out)
-    CU(cudaMemcpyAsync(gains_out, ctx->sel.gains, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  unsigned long long cov = 0;
-  CU(cudaMemcpyAsync(&cov, ctx->sel.covered_total, sizeof cov, cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  if (covered_out) *covered_out = cov;
+  // a one-slot batched selection, configured for this graph and the largest k asked so far
+  if (!ctx->msel || ctx->msel_n != ctx->g.n || ctx->msel_k < k) {
+    delete ctx->msel;
+    ctx->msel = new (std::nothrow) MultiSelect();
+    if (!ctx->msel) return set_err(ctx, GIM_ERR_OOM, "selection state");
+    const uint32_t kc = std::max(k, ctx->msel_n == ctx->g.n ? ctx->msel_k : 0u);
+    ctx->msel_n = ctx->g.n;
+    ctx->msel_k = 0;
+    gim_status st = ctx->msel->configure(ctx, {ctx->g.n}, {kc});
+    if (st != GIM_OK) return st;
+    ctx->msel_k = kc;
+  }
+  SelInput x;
+  x.active = true;
+  x.R = ctx->R;
+  x.Z = ctx->Z;
+  x.members = ctx->st.members;
+  x.rr_start = ctx->st.rr_start;
+  x.rr_len = ctx->st.rr_len;
+  x.cnt = ctx->st.cnt;
+  x.buf = &ctx->sel;
+  x.k = k;
+  std::vector<unsigned long long> cov;
+  std::vector<uint32_t> seeds, gains;
+  gim_status st = ctx->msel->run(ctx, {x}, ctx->stream, cov, seeds, gains_out ? &gains : nullptr);
+  if (st != GIM_OK) return st;
+  std::memcpy(seeds_out, seeds.data(), k * sizeof(uint32_t));
+  if (gains_out) std::memcpy(gains_out, gains.data(), k * sizeof(uint32_t));
+  if (covered_out) *covered_out = cov[0];
   return GIM_OK;
 }
 
@@ -131,6 +157,8 @@ void gim_destroy(gim_ctx *ctx) {
   dfree(ctx->st.rr_len);
   dfree(ctx->st.cnt);
   free_select(ctx->sel);
+  delete ctx->msel;
+  ctx->msel = nullptr;
   if (ctx->shared_held) shared_release(ctx->device);
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -174,6 +202,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   if ((e = cudaMalloc(&g.src, m_pad * 4)) != cudaSuccess) return bail(e, "alloc sources");
   if ((e = cudaMalloc(&g.thr, m_pad * 4)) != cudaSuccess) return bail(e, "alloc thresholds");
   if ((e = cudaMalloc(&g.rthr, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row thresholds");
+  if ((e = cudaMalloc(&g.rw, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row weights");
   if ((e = cudaMalloc(&g.cum, std::max<uint64_t>(m, 1) * 8)) != cudaSuccess) return bail(e, "alloc lt thresholds");
   if ((e = cudaMalloc(&d_w, std::max<uint64_t>(m, 1) * 4)) != cudaSuccess) return bail(e, "alloc weights");
   if ((e = cudaMalloc(&d_flags, 4)) != cudaSuccess) return bail(e, "alloc flags");
@@ -384,6 +413,10 @@ gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value) {
     ctx->group_budget = (uint32_t)std::min<uint64_t>(value, 0xFFFFFFFEull);
     return GIM_OK;
   }
+  if (opt == GIM_OPT_LARGE_PASS_BYTES && value > 0) {
+    ctx->big_budget = value;
+    return GIM_OK;
+  }
   return set_err(ctx, GIM_ERR_ARG, "unknown option or zero value");
 }
 
@@ -391,6 +424,10 @@ gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value) {
   if (!ctx || !value) return GIM_ERR_ARG;
   if (opt == GIM_OPT_GROUP_BUDGET) {
     *value = ctx->group_budget;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_LARGE_PASS_BYTES) {
+    *value = ctx->big_budget;
     return GIM_OK;
   }
   return set_err(ctx, GIM_ERR_ARG, "unknown option");
@@ -473,6 +510,16 @@ gim_status gim_reset_timings(gim_ctx *ctx) {
   if (!ctx) return GIM_ERR_ARG;
   ctx->t_kernel_ms[0] = ctx->t_kernel_ms[1] = 0;
   ctx->n_kernel[0] = ctx->n_kernel[1] = 0;
+  ctx->sel_kernel_ms = ctx->sel_bytes = ctx->sel_calls = ctx->sel_cov_members = 0;
+  return GIM_OK;
+}
+
+gim_status gim_selection_stats(gim_ctx *ctx, double out[4]) {
+  if (!ctx || !out) return GIM_ERR_ARG;
+  out[0] = ctx->sel_kernel_ms;
+  out[1] = ctx->sel_bytes;
+  out[2] = ctx->sel_calls;
+  out[3] = ctx->sel_cov_members;
   return GIM_OK;
 }
 

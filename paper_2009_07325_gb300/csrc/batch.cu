@@ -7,10 +7,13 @@
 // model whose work items are (instance, rr_id) pairs (sample.cu). The
 // selection of all instances runs as multi-instance kernels: every kernel
 // covers all instances, each block (or warp) finding its instance from
-// fixed block ranges, so a round of the greedy (argmax + cover) is two
-// launches for the whole batch. That fixed launch sequence is captured once
-// into a CUDA graph and replayed every round; the per-round inputs (set
-// counts, buffers) are read from a descriptor table in device memory.
+// fixed block ranges. The preparation (counts, inverted index) is a fixed
+// launch sequence, captured once into a CUDA graph and replayed every round;
+// the per-round inputs (set counts, buffers) are read from a descriptor
+// table in device memory. The k greedy rounds of every instance then run in
+// one cooperative launch of the persistent greedy kernel (greedy.cu), each
+// instance in its own block group, so instances with small k or small
+// graphs finish without waiting for the others.
 // The host advances each instance's IMM state machine between rounds.
 // Every instance's seeds, theta, LB and RR collection are those gim_imm
 // computes for it alone.
@@ -44,15 +47,21 @@ struct SelDesc {
   uint64_t *inv_off;
   uint32_t *cursor;
   uint32_t *inv;
-  uint8_t *covered;
+  uint32_t *covered;                      // words of the covered bitmap
+  uint32_t words;                         // ceil(R/32)
+  uint32_t hub_min;                       // a vertex in at least this many sets is a hub
+  uint8_t *hslot;                         // n: hub slot or 0xFF
+  uint32_t *hbits;                        // hub rows of `words` words
+  uint32_t *hmeta;                        // hub count, ids, counts + 1
+  unsigned int *err;                      // bit 1: more hubs than kHeavyCap (cannot happen: see hub_min)
   unsigned long long *best;               // k argmax keys
   uint32_t *seeds;                        // k (into the batch's packed seeds)
   uint32_t *gains;                        // k (packed)
   unsigned long long *covered_total;      // one (packed)
+  unsigned long long *stats;              // two (packed): see GreedyDesc::stats
   uint64_t *tile_sum;                     // tiles
+  unsigned int *bar;                      // greedy group barrier
   uint32_t tile_begin, tiles;             // scan blocks of this instance
-  uint32_t am_begin, am_blocks;           // argmax blocks
-  uint32_t cv_begin, cv_blocks;           // cover blocks
 };
 
 // Instance of block b: the last i with begin(i) <= b.
@@ -106,14 +115,23 @@ __device__ __forceinline__ unsigned long long block_excl(unsigned long long v, u
   return t;
 }
 
-// Clears covered flags, argmax slots and covered counts of active instances.
+// Clears covered flags, argmax slots, covered counts and the greedy group
+// barrier of active instances (blockIdx.y: instance, blockIdx.x: chunk).
 __global__ void __launch_bounds__(kSelThreads) bsel_clear(const SelDesc *d, uint32_t ni) {
-  for (uint32_t i = blockIdx.x; i < ni; i += gridDim.x) {
+  for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
     const SelDesc &D = d[i];
     if (!D.active) continue;
-    for (uint64_t t = threadIdx.x; t < D.R; t += blockDim.x) D.covered[t] = 0;
-    for (uint32_t t = threadIdx.x; t < D.k; t += blockDim.x) D.best[t] = 0ull;
-    if (threadIdx.x == 0) *D.covered_total = 0ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < D.words; t += stride) D.covered[t] = 0u;
+    if (blockIdx.x == 0) {
+      for (uint32_t t = threadIdx.x; t < D.k; t += blockDim.x) D.best[t] = 0ull;
+      if (threadIdx.x == 0) {
+        *D.covered_total = 0ull;
+        D.stats[0] = D.stats[1] = 0ull;
+        *D.bar = 0u;
+        D.hmeta[0] = 0u;
+      }
+    }
   }
 }
 
@@ -155,7 +173,10 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_sums(const SelDesc *d, 
   const uint64_t base = (uint64_t)(blockIdx.x - D.tile_begin) * kTile + (uint64_t)threadIdx.x * kTileItems;
   unsigned long long s = 0;
   for (uint32_t t = 0; t < kTileItems; ++t)
-    if (base + t < D.n) s += D.cnt[base + t];
+    if (base + t < D.n) {
+      const uint32_t c = D.cnt[base + t];
+      s += c < D.hub_min ? c : 0u;        // hubs have no inverted list
+    }
   unsigned long long ex;
   const unsigned long long tot = block_excl(s, &ex);
   if (threadIdx.x == 0) D.tile_sum[blockIdx.x - D.tile_begin] = tot;
@@ -178,7 +199,10 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_scan(const SelDesc *d, 
   }
 }
 
-// inv_off = exclusive scan of cnt; cnt_work = cnt + 1 (all unselected); cursor = 0.
+// Splits the vertices: a hub (count >= hub_min) takes the next hub slot,
+// with its id and count + 1 in hmeta; a light vertex keeps count + 1 in
+// cnt_work and gets its inverted list's offset (exclusive scan of the light
+// counts) and a zero cursor.
 __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint32_t ni) {
   const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
   const SelDesc &D = d[i];
@@ -189,23 +213,53 @@ __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint
   unsigned long long s = 0;
   for (uint32_t t = 0; t < kTileItems; ++t) {
     v[t] = base + t < D.n ? D.cnt[base + t] : 0u;
-    s += v[t];
+    s += v[t] < D.hub_min ? v[t] : 0u;
   }
   unsigned long long ex;
   block_excl(s, &ex);
   unsigned long long run = D.tile_sum[tile] + ex;
   for (uint32_t t = 0; t < kTileItems; ++t) {
-    if (base + t < D.n) {
-      D.inv_off[base + t] = run;
-      D.cnt_work[base + t] = v[t] + 1u;
-      D.cursor[base + t] = 0u;
+    const uint64_t x = base + t;
+    const bool hub = v[t] >= D.hub_min;
+    if (x < D.n) {
+      D.inv_off[x] = run;
+      D.cursor[x] = 0u;
+      uint8_t hs = 0xFFu;
+      uint32_t cw = v[t] + 1u;
+      if (hub) {
+        const uint32_t slot = atomicAdd(D.hmeta, 1u);
+        if (slot < kHeavyCap) {
+          D.hmeta[1 + slot] = (uint32_t)x;
+          D.hmeta[1 + kHeavyCap + slot] = v[t] + 1u;
+          hs = (uint8_t)slot;
+        } else {
+          atomicOr(D.err, 2u);
+        }
+        cw = 0u;
+      }
+      D.hslot[x] = hs;
+      D.cnt_work[x] = cw;
     }
-    run += v[t];
-    if (base + t + 1 == D.n) D.inv_off[D.n] = run;
+    run += hub ? 0u : v[t];
+    if (x + 1 == D.n) D.inv_off[D.n] = run;
   }
 }
 
-// inv: for every set j of every instance, j is appended to the list of each member.
+// Zeroes the bitmap rows of the hubs found (blockIdx.y: instance).
+__global__ void __launch_bounds__(kSelThreads) bsel_hub_clear(const SelDesc *d, uint32_t ni) {
+  for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
+    const SelDesc &D = d[i];
+    if (!D.active) continue;
+    const uint32_t H = D.hmeta[0] < kHeavyCap ? D.hmeta[0] : kHeavyCap;
+    const uint64_t total = (uint64_t)H * D.words;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total; t += stride) D.hbits[t] = 0u;
+  }
+}
+
+// For every set j of every instance: j is appended to the inverted list of
+// each light member and set in the bitmap row of each hub member (one warp
+// per set).
 __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint32_t ni) {
   const unsigned long long total = d[ni - 1].set_begin + d[ni - 1].R;   // this round's sets over the batch
   const uint32_t lane = threadIdx.x & 31u;
@@ -217,93 +271,33 @@ __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint3
     const uint64_t j = g - D.set_begin;
     const uint64_t b = D.rr_start[j];
     const uint32_t len = D.rr_len[j];
-    for (uint32_t t = lane; t < len; t += 32) {
-      const uint32_t x = D.members[b + t];
-      const uint32_t c = atomicAdd(&D.cursor[x], 1u);
-      D.inv[D.inv_off[x] + c] = (uint32_t)j;
-    }
-  }
-}
-
-__device__ __forceinline__ unsigned long long key_of(uint32_t cw, uint32_t x) {
-  return ((unsigned long long)cw << 32) | (unsigned long long)(~x);
-}
-
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    const bool hubs = D.hmeta[0] != 0u;
+    // four members per lane in flight: the cursor atomics return a value, so
+    // the loop is bound by their latency
+    for (uint32_t t0 = 0; t0 < len; t0 += 128) {
+      uint32_t x[4], hs[4], c[4];
+      uint64_t o[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long t = __shfl_xor_sync(kFullMask, v, o);
-    v = t > v ? t : v;
-  }
-  return v;
-}
-
-// Round t of every instance that still selects: best[t] = max key.
-__global__ void __launch_bounds__(kSelThreads) bsel_argmax(const SelDesc *d, uint32_t ni, uint32_t t) {
-  __shared__ unsigned long long part[kSelThreads / 32];
-  const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.am_begin; });
-  const SelDesc &D = d[i];
-  if (!D.active || t >= D.k) return;
-  unsigned long long m = 0;
-  const uint32_t lb = blockIdx.x - D.am_begin;
-  for (uint32_t x = lb * blockDim.x + threadIdx.x; x < D.n; x += D.am_blocks * blockDim.x) {
-    const unsigned long long a = key_of(D.cnt_work[x], x);
-    m = a > m ? a : m;
-  }
-  m = warp_max_u64(m);
-  if ((threadIdx.x & 31u) == 0) part[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    m = threadIdx.x < kSelThreads / 32 ? part[threadIdx.x] : 0ull;
-    m = warp_max_u64(m);
-    if (threadIdx.x == 0) atomicMax(&D.best[t], m);
-  }
-}
-
-// Round t: record the chosen seed, mark it selected, cover its uncovered sets.
-__global__ void __launch_bounds__(kSelThreads) bsel_cover(const SelDesc *d, uint32_t ni, uint32_t t) {
-  __shared__ unsigned long long part[kSelThreads / 32];
-  const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.cv_begin; });
-  const SelDesc &D = d[i];
-  const uint32_t lb = blockIdx.x - D.cv_begin;
-  if (!D.active || t >= D.k) return;
-  const unsigned long long key = D.best[t];
-  const uint32_t u = ~(uint32_t)(key & 0xFFFFFFFFull);
-  const uint32_t cw = (uint32_t)(key >> 32);
-  if (lb == 0 && threadIdx.x == 0) {
-    D.seeds[t] = u;
-    D.gains[t] = cw ? cw - 1u : 0u;
-    D.cnt_work[u] = 0u;   // selected; no other thread writes cnt_work[u] in this round
-  }
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = (lb * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (D.cv_blocks * blockDim.x) >> 5;
-  const uint64_t i0 = D.inv_off[u], i1 = D.inv_off[u + 1];
-  unsigned long long newly = 0;
-  for (uint64_t p = i0 + warp; p < i1; p += nwarps) {
-    const uint32_t j = D.inv[p];
-    uint32_t was = 1;
-    if (lane == 0) {
-      was = D.covered[j];
-      if (!was) D.covered[j] = 1;
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t t = t0 + 32 * q + lane;
+        x[q] = t < len ? D.members[b + t] : 0xFFFFFFFFu;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) hs[q] = (hubs && x[q] != 0xFFFFFFFFu) ? D.hslot[x[q]] : 0xFFu;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (x[q] == 0xFFFFFFFFu) continue;
+        if (hs[q] != 0xFFu) {
+          atomicOr(D.hbits + (uint64_t)hs[q] * D.words + (j >> 5), 1u << (j & 31u));
+        } else {
+          c[q] = atomicAdd(&D.cursor[x[q]], 1u);
+          o[q] = D.inv_off[x[q]];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (x[q] != 0xFFFFFFFFu && hs[q] == 0xFFu) D.inv[o[q] + c[q]] = (uint32_t)j;
     }
-    was = __shfl_sync(kFullMask, was, 0);
-    if (was) continue;
-    newly += (lane == 0);
-    const uint64_t b = D.rr_start[j];
-    const uint32_t len = D.rr_len[j];
-    for (uint32_t q = lane; q < len; q += 32) {
-      const uint32_t x = D.members[b + q];
-      if (x != u) atomicSub(&D.cnt_work[x], 1u);
-    }
-  }
-  const unsigned long long s = warp_sum_u64(newly);
-  if (lane == 0) part[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long tot = 0;
-    for (uint32_t w = 0; w < kSelThreads / 32; ++w) tot += part[w];
-    if (tot) atomicAdd(D.covered_total, tot);
   }
 }
 
@@ -326,22 +320,20 @@ cudaError_t ensure_buf(T *&p, uint64_t &cap, uint64_t need) {
   return cudaSuccess;
 }
 
-// The fixed launch sequence of a batched selection: counts (for instances
-// that count a prefix), index build, max_k greedy rounds.
-cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uint32_t am_blocks,
-                              uint32_t cv_blocks, uint32_t fill_blocks, uint32_t max_k, uint32_t cnt_blocks,
-                              cudaStream_t s) {
-  bsel_clear<<<ni, kSelThreads, 0, s>>>(d, ni);
-  bsel_cnt_clear<<<dim3(cnt_blocks, std::min<uint32_t>(ni, 65535)), kSelThreads, 0, s>>>(d, ni);
+// The fixed launch sequence that prepares a batched selection: counts (for
+// instances that count a prefix) and the inverted index. The greedy rounds
+// follow as cooperative launches of the greedy kernel (greedy.cu).
+cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uint32_t fill_blocks,
+                              uint32_t cnt_blocks, cudaStream_t s) {
+  const uint32_t ny = std::min<uint32_t>(ni, 65535);
+  bsel_clear<<<dim3(64, ny), kSelThreads, 0, s>>>(d, ni);
+  bsel_cnt_clear<<<dim3(cnt_blocks, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_count<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
   bsel_tile_sums<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
   bsel_tile_scan<<<ni, kSelThreads, 0, s>>>(d, ni);
   bsel_apply<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_hub_clear<<<dim3(128, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_fill<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
-  for (uint32_t t = 0; t < max_k; ++t) {
-    bsel_argmax<<<am_blocks, kSelThreads, 0, s>>>(d, ni, t);
-    bsel_cover<<<cv_blocks, kSelThreads, 0, s>>>(d, ni, t);
-  }
   return cudaGetLastError();
 }
 
@@ -397,18 +389,28 @@ struct MultiSelect::Impl {
   uint32_t *seeds = nullptr;             // packed, sum of k
   uint32_t *gains = nullptr;
   unsigned long long *covered = nullptr; // one per slot
+  unsigned long long *stats = nullptr;   // two per slot
+  std::vector<unsigned long long> h_stats;
   std::vector<uint64_t> seed_off;
   std::vector<uint32_t> k_cfg;
-  uint32_t ni = 0, scan_blocks = 0, am_blocks = 0, cv_blocks = 0, max_k = 0, fill_blocks = 0, cnt_blocks = 0;
+  uint32_t ni = 0, scan_blocks = 0, fill_blocks = 0, cnt_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // greedy rounds: block groups, and the waves of instances that share one cooperative launch
+  std::vector<GreedyDesc> gh;
+  GreedyDesc *gd = nullptr;
+  unsigned int *sync = nullptr;          // ni group barriers, then the error flag
+  std::vector<uint32_t> wave_first, wave_grid;
   ~Impl() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (gd) cudaFree(gd);
+    if (sync) cudaFree(sync);
     if (d) cudaFree(d);
     if (seeds) cudaFree(seeds);
     if (gains) cudaFree(gains);
     if (covered) cudaFree(covered);
+    if (stats) cudaFree(stats);
   }
 };
 
@@ -421,7 +423,8 @@ gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, 
   B.h.assign(B.ni, SelDesc{});
   B.seed_off.assign(B.ni + 1, 0);
   B.k_cfg = k;
-  uint32_t tiles = 0, am = 0, cv = 0, nmax = 0;
+  uint32_t tiles = 0, nmax = 0;
+  double nsum = 0;
   for (uint32_t i = 0; i < B.ni; ++i) {
     SelDesc &D = B.h[i];
     D.n = n[i];
@@ -429,33 +432,57 @@ gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, 
     D.tile_begin = tiles;
     D.tiles = (D.n + kTile - 1) / kTile;
     tiles += D.tiles;
-    D.am_begin = am;
-    D.am_blocks = std::max<uint32_t>(1, std::min<uint32_t>((D.n + 4095) / 4096, 64));
-    am += D.am_blocks;
-    // cover parallelism grows with the graph: a hub seed covers a large share of the sets
-    D.cv_begin = cv;
-    D.cv_blocks = std::max<uint32_t>(8, std::min<uint32_t>((D.n + 65535) / 65536, 256));
-    cv += D.cv_blocks;
     B.seed_off[i + 1] = B.seed_off[i] + D.k;
-    B.max_k = std::max(B.max_k, D.k);
     nmax = std::max(nmax, D.n);
+    nsum += D.n;
   }
   B.scan_blocks = tiles;
-  B.am_blocks = am;
-  B.cv_blocks = cv;
   B.fill_blocks = (uint32_t)ctx->sm_count * 8;
   B.cnt_blocks = std::max<uint32_t>(1, std::min<uint32_t>((nmax + 4095) / 4096, 256));
+
+  // greedy block groups: in proportion to n (the argmax reads all n counts
+  // every round), at least one block and about 8K vertices per block at
+  // least; instances are packed into waves of at most G blocks
+  const uint32_t G = greedy_max_blocks(ctx->sm_count);
+  B.gh.assign(B.ni, GreedyDesc{});
+  B.wave_first.clear();
+  B.wave_grid.clear();
+  uint32_t cur = 0;
+  for (uint32_t i = 0; i < B.ni; ++i) {
+    GreedyDesc &g = B.gh[i];
+    const double share = nsum > 0 ? (double)G * n[i] / nsum : 1.0;
+    uint32_t nb = (uint32_t)std::max(1.0, std::floor(share));
+    nb = std::min<uint32_t>(nb, std::max<uint32_t>(1, (n[i] + 8191) / 8192));
+    nb = std::min(nb, G);
+    if (B.wave_first.empty() || cur + nb > G) {
+      B.wave_first.push_back(i);
+      B.wave_grid.push_back(0);
+      cur = 0;
+    }
+    g.n = n[i];
+    g.g_begin = cur;
+    g.g_blocks = nb;
+    cur += nb;
+    B.wave_grid.back() = cur;
+  }
+  CU(cudaMalloc(&B.gd, std::max<uint32_t>(B.ni, 1) * sizeof(GreedyDesc)));
+  CU(cudaMalloc(&B.sync, (B.ni + 1) * sizeof(unsigned int)));
   CU(cudaMalloc(&B.d, std::max<uint32_t>(B.ni, 1) * sizeof(SelDesc)));
   CU(cudaMalloc(&B.seeds, std::max<uint64_t>(B.seed_off[B.ni], 1) * 4));
   CU(cudaMalloc(&B.gains, std::max<uint64_t>(B.seed_off[B.ni], 1) * 4));
   CU(cudaMalloc(&B.covered, std::max<uint32_t>(B.ni, 1) * 8ull));
+  CU(cudaMalloc(&B.stats, std::max<uint32_t>(B.ni, 1) * 16ull));
+  B.h_stats.assign(2 * (size_t)std::max<uint32_t>(B.ni, 1), 0ull);
   return GIM_OK;
 }
 
 uint64_t MultiSelect::seed_offset(uint32_t i) const { return p->seed_off[i]; }
+uint32_t MultiSelect::slots() const { return p->ni; }
+uint32_t MultiSelect::k_of(uint32_t i) const { return p->k_cfg[i]; }
 
 gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaStream_t s,
-                            std::vector<unsigned long long> &cov, std::vector<uint32_t> &seeds) {
+                            std::vector<unsigned long long> &cov, std::vector<uint32_t> &seeds,
+                            std::vector<uint32_t> *gains) {
   Impl &B = *p;
   unsigned long long total_sets = 0, total_counted = 0;
   for (uint32_t i = 0; i < B.ni; ++i) {
@@ -472,17 +499,28 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     total_sets += x.R;
     SelectBuffers &b = *x.buf;
     const uint32_t *own_before = b.cnt_own;
-    if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || (!x.cnt && !b.cnt_own)) {
-      uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap, c3 = b.n_cap;
+    if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || !b.hslot ||
+        (!x.cnt && !b.cnt_own)) {   // the n-sized buffers share n_cap
+      uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap, c3 = b.n_cap, c4 = b.n_cap;
       CU(ensure_buf(b.cnt_work, c0, (uint64_t)D.n + 4));
       CU(ensure_buf(b.inv_off, c1, (uint64_t)D.n + 4));
       CU(ensure_buf(b.cursor, c2, (uint64_t)D.n + 4));
+      CU(ensure_buf(b.hslot, c4, (uint64_t)D.n + 4));
       if (!x.cnt) CU(ensure_buf(b.cnt_own, c3, (uint64_t)D.n + 4));
-      b.n_cap = std::min(c0, std::min(c1, c2));
+      b.n_cap = std::min(std::min(c0, c4), std::min(c1, c2));
       if (!x.cnt) b.n_cap = std::min(b.n_cap, c3);
     }
+    // A hub is a vertex in at least hub_min sets: at least R/32 (its bitmap
+    // row is no longer than its inverted list would be) and at least
+    // Z/kHeavyCap, so that the counts (summing to at most Z) admit at most
+    // kHeavyCap hubs.
+    D.words = (uint32_t)((x.R + 31) / 32);
+    const uint64_t hm = std::max<uint64_t>(std::max<uint64_t>((x.R + 31) / 32, (x.Z + kHeavyCap - 1) / kHeavyCap), 1);
+    D.hub_min = (uint32_t)std::min<uint64_t>(hm, 0xFFFFFFFFull);
     CU(ensure_buf(b.inv, b.z_cap, std::max<uint64_t>(x.Z, 1)));
-    CU(ensure_buf(b.covered, b.r_cap, std::max<uint64_t>(x.R, 1)));
+    CU(ensure_buf(b.covered, b.r_cap, std::max<uint64_t>(D.words, 1)));
+    CU(ensure_buf(b.hbits, b.hb_cap, (uint64_t)kHeavyCap * std::max<uint32_t>(D.words, 1)));
+    if (!b.hmeta) CU(cudaMalloc(&b.hmeta, (1 + 2 * kHeavyCap) * sizeof(uint32_t)));
     if (b.k_cap < D.k || !b.best || !b.seeds || !b.gains) {   // the three k-sized buffers share k_cap
       uint64_t k0 = b.k_cap, k1 = b.k_cap, k2 = b.k_cap;
       CU(ensure_buf(b.best, k0, D.k));
@@ -511,15 +549,44 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     D.seeds = B.seeds + B.seed_off[i];
     D.gains = B.gains + B.seed_off[i];
     D.covered_total = B.covered + i;
+    D.stats = B.stats + 2 * i;
     D.tile_sum = b.scan_tmp;
+    D.bar = B.sync + i;
+    D.hslot = b.hslot;
+    D.hbits = b.hbits;
+    D.hmeta = b.hmeta;
+    D.err = B.sync + B.ni;
+  }
+  for (uint32_t i = 0; i < B.ni; ++i) {
+    const SelDesc &D = B.h[i];
+    GreedyDesc &g = B.gh[i];
+    g.k = D.active ? D.k : 0u;
+    if (!D.active) continue;
+    g.words = D.words;
+    g.cnt_work = D.cnt_work;
+    g.inv_off = D.inv_off;
+    g.inv = D.inv;
+    g.covered = D.covered;
+    g.hslot = D.hslot;
+    g.hbits = D.hbits;
+    g.hmeta = D.hmeta;
+    g.members = D.members;
+    g.rr_start = D.rr_start;
+    g.rr_len = D.rr_len;
+    g.best = D.best;
+    g.seeds = D.seeds;
+    g.gains = D.gains;
+    g.covered_total = D.covered_total;
+    g.stats = D.stats;
+    g.bar = D.bar;
   }
   CU(cudaMemcpyAsync(B.d, B.h.data(), B.ni * sizeof(SelDesc), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(B.gd, B.gh.data(), B.ni * sizeof(GreedyDesc), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(B.sync + B.ni, 0, sizeof(unsigned int), s));
   if (!B.exec) {
     // the launch sequence is fixed for these slots; the round's inputs live in B.d
     CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t ce =
-        enqueue_selection(B.d, B.ni, B.scan_blocks, B.am_blocks, B.cv_blocks, B.fill_blocks, B.max_k, B.cnt_blocks,
-                          s);
+    const cudaError_t ce = enqueue_selection(B.d, B.ni, B.scan_blocks, B.fill_blocks, B.cnt_blocks, s);
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s, &g);
     if (ce != cudaSuccess) return cuda_err(ctx, ce, "selection capture");
@@ -527,13 +594,45 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     B.graph = g;
     CU(cudaGraphInstantiate(&B.exec, B.graph, 0));
   }
+  CU(cudaEventRecord(ctx->ev[8], s));
   CU(cudaGraphLaunch(B.exec, s));
-  ctx->launches += 7 + 2ull * B.max_k;
+  ctx->launches += 8;
+  for (size_t w = 0; w < B.wave_first.size(); ++w) {
+    const uint32_t first = B.wave_first[w];
+    const uint32_t count = (w + 1 < B.wave_first.size() ? B.wave_first[w + 1] : B.ni) - first;
+    CU(launch_greedy(B.gd + first, count, B.wave_grid[w], B.sync + B.ni, s));
+    ctx->launches += 1;
+  }
+  CU(cudaEventRecord(ctx->ev[9], s));
   cov.resize(B.ni);
   seeds.resize(B.seed_off[B.ni]);
+  if (gains) gains->resize(B.seed_off[B.ni]);
+  unsigned int flags = 0;
+  CU(cudaMemcpyAsync(B.h_stats.data(), B.stats, B.ni * 16ull, cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(cov.data(), B.covered, B.ni * 8ull, cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(seeds.data(), B.seeds, B.seed_off[B.ni] * 4, cudaMemcpyDeviceToHost, s));
+  if (gains) CU(cudaMemcpyAsync(gains->data(), B.gains, B.seed_off[B.ni] * 4, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&flags, B.sync + B.ni, sizeof flags, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  if (flags & 2u) return set_err(ctx, GIM_ERR_STATE, "greedy selection: more hubs than slots");
+  if (flags) return set_err(ctx, GIM_ERR_TIMEOUT, "greedy selection: a block barrier wait gave up");
+  // device time and algorithmic bytes: reading the store and writing the
+  // index (8 per member) and scanning the counts (4 per vertex); then per
+  // round reading all counts (4 per vertex), the seed's list or row (4 per
+  // word) and, per member of a newly covered set, its id (4) and a count
+  // read-modify-write (8); plus the covered bitmap
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ctx->ev[8], ctx->ev[9]);
+  ctx->sel_kernel_ms += ms;
+  ctx->sel_calls += 1;
+  for (uint32_t i = 0; i < B.ni; ++i) {
+    const SelDesc &D = B.h[i];
+    if (!D.active) continue;
+    const double n = D.n, Z = (double)in[i].Z;
+    ctx->sel_bytes += 8.0 * Z + 4.0 * n + (double)D.k * 4.0 * n + 4.0 * (double)B.h_stats[2 * i + 1] +
+                      12.0 * (double)B.h_stats[2 * i] + 4.0 * D.words;
+    ctx->sel_cov_members += (double)B.h_stats[2 * i];
+  }
   return GIM_OK;
 }
 

@@ -36,7 +36,6 @@ gim_status cuda_err(gim_ctx *ctx, cudaError_t e, const char *what) {
 
 namespace {
 
-constexpr uint64_t kBigBudget = 8ull << 30;     // bytes of large-pass scratch (bitmaps + queues)
 constexpr uint64_t kInitialStore = 1ull << 24;  // store entries at first use
 
 DeviceShared g_shared[kMaxDevices];
@@ -148,14 +147,15 @@ namespace {
 
 // Large-pass scratch for graphs of up to n vertices (bitmap + n-entry queue per slot).
 gim_status ensure_big(gim_ctx *ctx, DeviceShared &D, uint32_t n) {
-  if (D.big.slots && D.big.n_cap >= n) return GIM_OK;
+  const uint64_t budget = ctx->big_budget;
+  if (D.big.slots && D.big.n_cap >= n && D.big_budget == budget) return GIM_OK;
   dfree(D.big.bitmap);
   dfree(D.big.queue);
   D.big = BigScratch{};
   const uint64_t words = ((uint64_t)n + 31) / 32;
   const uint64_t wps = (words + 31) / 32 * 32;
   const uint64_t per = wps * 4 + (uint64_t)n * 4;
-  uint64_t slots = std::min<uint64_t>(kBigBudget / std::max<uint64_t>(per, 1), (uint64_t)D.sm_count * 4);
+  uint64_t slots = std::min<uint64_t>(budget / std::max<uint64_t>(per, 1), (uint64_t)D.sm_count * 8);
   slots = std::max<uint64_t>(slots, 1);
   CU(cudaMalloc(&D.big.bitmap, wps * 4 * slots));
   CU(cudaMalloc(&D.big.queue, (uint64_t)n * 4 * slots));
@@ -163,6 +163,7 @@ gim_status ensure_big(gim_ctx *ctx, DeviceShared &D, uint32_t n) {
   D.big.words_per_slot = wps;
   D.big.n_cap = n;
   D.big.slots = (uint32_t)slots;
+  D.big_budget = budget;
   return GIM_OK;
 }
 
@@ -212,6 +213,7 @@ void fill_desc(InstDesc &d, gim_ctx *c, uint64_t seed, uint64_t item_begin) {
   d.src = c->g.src;
   d.thr = c->g.thr;
   d.rthr = c->g.rthr;
+  d.rw = c->g.rw;
   d.cum = c->g.cum;
   d.members = c->st.members;
   d.store_cap = c->st.cap;

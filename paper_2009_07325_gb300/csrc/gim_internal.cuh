@@ -24,7 +24,7 @@ struct PhiloxKey {
   uint32_t k0, k1;
 };
 
-__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, PhiloxKey key) {
+__host__ __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, PhiloxKey key) {
   uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
@@ -45,6 +45,58 @@ __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
 
 enum : uint32_t { kTagRoot = 0, kTagEdge = 1, kTagStep = 2 };
 
+// The IC coin words of in-edge group g in RR set j are
+// philox10(g, kTagEdge, j_lo, j_hi, key). Three of the four counter words
+// are fixed for the whole set, so everything of rounds 1 and 2 that does not
+// depend on g is computed once per set (coin_key) and a group costs one
+// 32x32 multiply in each of those rounds instead of two. coin_words(g, ck)
+// equals philox10(g, kTagEdge, j_lo, j_hi, key) bit for bit.
+struct CoinKey {
+  uint32_t c, d, e, f;   // round-1 c2 mask, round-2 c0 mask, round-2 c2 mask, round-2 c3
+  PhiloxKey k2;          // the key after two rounds
+};
+
+__host__ __device__ __forceinline__ CoinKey coin_key(uint32_t jlo, uint32_t jhi, PhiloxKey key) {
+  const unsigned long long b1 = (unsigned long long)0xCD9E8D57u * jlo;
+  const uint32_t c0r1 = (uint32_t)(b1 >> 32) ^ kTagEdge ^ key.k0;   // c0 after round 1
+  const uint32_t c1r1 = (uint32_t)b1;                               // c1 after round 1
+  const uint32_t k0b = key.k0 + 0x9E3779B9u, k1b = key.k1 + 0xBB67AE85u;
+  const unsigned long long a2 = (unsigned long long)0xD2511F53u * c0r1;
+  CoinKey ck;
+  ck.c = jhi ^ key.k1;
+  ck.d = c1r1 ^ k0b;
+  ck.e = (uint32_t)(a2 >> 32) ^ k1b;
+  ck.f = (uint32_t)a2;
+  ck.k2.k0 = k0b + 0x9E3779B9u;
+  ck.k2.k1 = k1b + 0xBB67AE85u;
+  return ck;
+}
+
+__host__ __device__ __forceinline__ uint4 coin_words(uint32_t g, const CoinKey &ck) {
+  const unsigned long long a1 = (unsigned long long)0xD2511F53u * g;   // round 1: only c0 varies
+  const uint32_t c2r1 = (uint32_t)(a1 >> 32) ^ ck.c;
+  const unsigned long long b2 = (unsigned long long)0xCD9E8D57u * c2r1;   // round 2: only c2 varies
+  uint32_t c0 = (uint32_t)(b2 >> 32) ^ ck.d;
+  uint32_t c1 = (uint32_t)b2;
+  uint32_t c2 = (uint32_t)a1 ^ ck.e;
+  uint32_t c3 = ck.f;
+  uint32_t k0 = ck.k2.k0, k1 = ck.k2.k1;
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const unsigned long long a = (unsigned long long)0xD2511F53u * c0;
+    const unsigned long long b = (unsigned long long)0xCD9E8D57u * c2;
+    const uint32_t y0 = (uint32_t)(b >> 32) ^ c1 ^ k0;
+    const uint32_t y2 = (uint32_t)(a >> 32) ^ c3 ^ k1;
+    c0 = y0;
+    c1 = (uint32_t)b;
+    c2 = y2;
+    c3 = (uint32_t)a;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
 // randSelect(V) of Alg. 3: the root of RR set j, high word of a 64-bit draw times n.
 __device__ __forceinline__ uint32_t draw_root(PhiloxKey key, uint64_t j, uint32_t n) {
   const uint4 r = philox10(0u, kTagRoot, (uint32_t)j, (uint32_t)(j >> 32), key);
@@ -63,6 +115,7 @@ struct DevGraph {
   uint32_t *thr = nullptr;   // same length: IC coin threshold ceil(w * 2^24)
   uint32_t *rthr = nullptr;  // n: the row's common threshold when all its in-edges share one, else kPerEdge
   uint64_t *cum = nullptr;   // m: LT cumulative thresholds in 2^-32 units
+  uint32_t *rw = nullptr;    // n: fp32 bits of the row's common weight when all its in-edges share one, else kPerEdge
 };
 
 constexpr uint32_t kPerEdge = 0xFFFFFFFFu;   // rthr value of a row whose thresholds differ
@@ -83,7 +136,7 @@ struct InstDesc {
   // graph
   uint32_t n;
   uint32_t pad0;
-  const uint32_t *off, *src, *thr, *rthr;
+  const uint32_t *off, *src, *thr, *rthr, *rw;
   const uint64_t *cum;
   // RR collection
   uint32_t *members;
@@ -136,7 +189,7 @@ struct CommonScratch {
 };
 
 // Scratch of the large-set passes: per slot an n-bit visited bitmap (all zero
-// between sets) and an n-entry queue. IC uses one 512-thread block per slot,
+// between sets) and an n-entry queue. IC uses one 256-thread block per slot,
 // LT one warp per slot.
 struct BigScratch {
   uint32_t *bitmap = nullptr;
@@ -146,7 +199,7 @@ struct BigScratch {
   uint32_t slots = 0;
 };
 
-constexpr int kBigBlock = 512;
+constexpr int kBigBlock = 256;
 
 // Host launchers (sample.cu).
 // `one` (nullable): the launch's only instance, passed by value so that the
@@ -165,24 +218,60 @@ int lt_common_blocks_per_sm();
 cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_flags, cudaStream_t s);
 enum : unsigned int { kGraphBadSource = 1u, kGraphNotAscending = 2u, kGraphBadWeight = 4u, kGraphNotLT = 8u };
 
-// Selection (select.cu).
+// Selection buffers of one instance (grown on demand, kept between calls).
+// Vertices that lie in many RR sets ("hubs": count >= a threshold chosen per
+// selection) get a bitmap over the sets instead of an inverted list, and
+// their counts live in a short array; the others ("light" vertices) get
+// inverted lists (batch.cu, greedy.cu).
+constexpr uint32_t kHeavyCap = 255;     // hubs per selection at most (slot ids fit a byte; 0xFF = light)
 struct SelectBuffers {
-  uint32_t *cnt_work = nullptr;  // n (count + 1 while unselected, 0 once selected)
+  uint32_t *cnt_work = nullptr;  // n: light count + 1 while unselected, 0 once selected or a hub
   uint64_t *inv_off = nullptr;   // n+1
   uint32_t *cursor = nullptr;    // n
   uint32_t *inv = nullptr;       // Z rr ids
-  uint8_t *covered = nullptr;    // R flags
+  uint32_t *covered = nullptr;   // ceil(R/32) words: bit j set once RR set j is covered
   unsigned long long *best = nullptr;   // k argmax keys
   uint32_t *seeds = nullptr;     // k
   uint32_t *gains = nullptr;     // k
   unsigned long long *covered_total = nullptr;
   uint64_t *scan_tmp = nullptr;  // block partial sums
   uint32_t *cnt_own = nullptr;   // n: counts over a prefix of a shared store (serving)
-  uint64_t n_cap = 0, z_cap = 0, r_cap = 0, k_cap = 0, scan_cap = 0;
+  uint8_t *hslot = nullptr;      // n: hub slot of a vertex, 0xFF if light
+  uint32_t *hbits = nullptr;     // kHeavyCap rows of ceil(R/32) words: bit j of row s = set j holds hub s
+  uint32_t *hmeta = nullptr;     // 1 + 2 kHeavyCap: hub count, hub ids, hub counts + 1 (0 once selected)
+  uint64_t n_cap = 0, z_cap = 0, r_cap = 0, k_cap = 0, scan_cap = 0, hb_cap = 0;
 };
 
-cudaError_t run_select(const DevGraph &g, const DevStore &st, uint64_t R, uint64_t Z, uint32_t k, SelectBuffers &b,
-                       int sm_count, cudaStream_t s, uint64_t *launches);
+// The k greedy rounds of one instance in the persistent greedy kernel
+// (greedy.cu). Blocks [g_begin, g_begin + g_blocks) of the launch serve it.
+struct GreedyDesc {
+  uint32_t n = 0, k = 0;                 // k = 0: nothing to select
+  uint32_t g_begin = 0, g_blocks = 0;
+  uint32_t words = 0;                    // ceil(R/32): covered bitmap words, hub row length
+  uint32_t *cnt_work = nullptr;          // n: light count + 1 while unselected, else 0
+  const uint64_t *inv_off = nullptr;     // n + 1 (hubs have empty lists)
+  const uint32_t *inv = nullptr;         // rr ids per light vertex
+  uint32_t *covered = nullptr;           // words, zero on entry
+  const uint8_t *hslot = nullptr;        // n: hub slot or 0xFF
+  const uint32_t *hbits = nullptr;       // hub rows
+  uint32_t *hmeta = nullptr;             // hub count, ids, counts + 1
+  const uint32_t *members = nullptr;
+  const uint64_t *rr_start = nullptr;
+  const uint32_t *rr_len = nullptr;
+  unsigned long long *best = nullptr;    // k argmax keys, zero on entry
+  uint32_t *seeds = nullptr;             // k
+  uint32_t *gains = nullptr;             // k
+  unsigned long long *covered_total = nullptr;   // zero on entry
+  unsigned long long *stats = nullptr;   // 2, zero on entry: members of newly covered sets, seed list/row words
+  unsigned int *bar = nullptr;           // group barrier counter, zero on entry
+};
+constexpr int kGreedyThreads = 512;
+// Blocks one cooperative launch of the greedy kernel may use on this device.
+uint32_t greedy_max_blocks(int sm_count);
+// Runs the greedy rounds of d[0..ni) (device array) as one cooperative
+// launch of `grid` blocks. *err (device, zero on entry) becomes nonzero if a
+// group barrier gave up waiting.
+cudaError_t launch_greedy(const GreedyDesc *d, uint32_t ni, uint32_t grid, unsigned int *err, cudaStream_t s);
 
 // Per-device state shared by every context of the device: sampling scratch
 // and launch tables. Its mutex serialises the sampling of all contexts that
@@ -195,6 +284,7 @@ struct DeviceShared {
   uint32_t lt_grid = 0;
   CommonScratch cs;
   BigScratch big;
+  uint64_t big_budget = 0;             // the budget `big` was sized for
   InstDesc *d_desc = nullptr;
   uint64_t desc_cap = 0;
   InstDesc *h_desc = nullptr;          // pinned
@@ -263,8 +353,12 @@ class MultiSelect {
   MultiSelect();
   ~MultiSelect();
   gim_status configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k);
+  // Runs one selection round of every active slot; cov, seeds (and gains)
+  // come back packed by slot (seed_offset).
   gim_status run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaStream_t s, std::vector<unsigned long long> &cov,
-                 std::vector<uint32_t> &seeds);
+                 std::vector<uint32_t> &seeds, std::vector<uint32_t> *gains = nullptr);
+  uint32_t slots() const;
+  uint32_t k_of(uint32_t i) const;
   uint64_t seed_offset(uint32_t i) const;
 
  private:
@@ -310,12 +404,17 @@ struct gim_ctx {
 
   bool shared_held = false;       // holds a reference on the device's shared scratch
   uint32_t group_budget = 1u << 14;   // GIM_OPT_GROUP_BUDGET
+  uint64_t big_budget = 16ull << 30;  // GIM_OPT_LARGE_PASS_BYTES
 
   gim::SelectBuffers sel;
+  gim::MultiSelect *msel = nullptr;   // gim_select_seeds / gim_imm: a one-slot batched selection
+  uint32_t msel_n = 0, msel_k = 0;
 
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[10] = {};
   double t_sample_ms = 0, t_select_ms = 0, t_wall_ms = 0, lb_rounds = 0;
   // sampling-kernel launches since the last reset of these counters
   double t_kernel_ms[2] = {0, 0};       // common-case pass, large-set pass
   double n_kernel[2] = {0, 0};
+  // selections since the last reset: device time, algorithmic bytes, calls, members of covered sets
+  double sel_kernel_ms = 0, sel_bytes = 0, sel_calls = 0, sel_cov_members = 0;
 };

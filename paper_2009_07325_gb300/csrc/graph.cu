@@ -60,7 +60,9 @@ __device__ __forceinline__ unsigned long long lt_round(double P) {
 }
 
 // Warp per row: ascending sources within the row, the row's common IC
-// threshold (rthr), and the LT thresholds
+// threshold (rthr), the row's common weight (rw: the fp32 bits when every
+// in-edge of the row carries the same weight, else kPerEdge), and the LT
+// thresholds
 //   cum[e_i] = min(2^32, round_half_up(P_i * 2^32)),
 // P_i the fp64 running sum of the row's weights in CSR order; a row summing
 // to within 1e-6 of 1 gets cum[last] = 2^32 so that it always selects an
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
                                                         const float *__restrict__ w,
                                                         const uint32_t *__restrict__ thr,
                                                         uint32_t *__restrict__ rthr, uint64_t *__restrict__ cum,
-                                                        unsigned int *__restrict__ flags) {
+                                                        uint32_t *__restrict__ rw, unsigned int *__restrict__ flags) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -85,7 +87,8 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
   for (uint32_t v = warp; v < n; v += nwarps) {
     const uint32_t s = off[v], e = off[v + 1];
     const uint32_t common0 = e > s ? thr[s] : 0u;
-    bool differs = false;
+    const uint32_t w0 = e > s ? __float_as_uint(w[s]) : kPerEdge;
+    bool differs = false, wdiffers = false;
     int emin = 0x7FFFFFFF;
     // pass 1: checks, smallest ulp exponent
     for (uint32_t base = s; base < e; base += 32) {
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
       const bool in = i < e;
       const uint32_t si = in ? src[i] : 0u;
       if (in && thr[i] != common0) differs = true;
+      if (in && __float_as_uint(w[i]) != w0) wdiffers = true;
       uint32_t prev = __shfl_up_sync(kFullMask, si, 1);
       if (lane == 0 && base > s) prev = src[base - 1];
       if (in && i > s && !(prev < si)) bad |= kGraphNotAscending;
@@ -154,8 +158,10 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
       }
     }
     const bool any_diff = __any_sync(kFullMask, differs);
+    const bool any_wdiff = __any_sync(kFullMask, wdiffers);
     if (lane == 0) {
       rthr[v] = any_diff ? kPerEdge : common0;
+      rw[v] = any_wdiff ? kPerEdge : w0;
       if (e > s && fabs(__dsub_rn(P, 1.0)) <= 1e-6) cum[e - 1] = 4294967296ull;
       if (P > 1.0 + 1e-6) bad |= kGraphNotLT;
     }
@@ -172,7 +178,7 @@ cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_fla
   if (e != cudaSuccess) return e;
   int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 7) / 8, 152ull * 16);
   if (rb < 1) rb = 1;
-  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, d_w, g.thr, g.rthr, g.cum, d_flags);
+  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, d_w, g.thr, g.rthr, g.cum, g.rw, d_flags);
   return cudaGetLastError();
 }
 

@@ -22,11 +22,11 @@
 //   each vertex is expanded once). The hash set is stamped with a per-set
 //   epoch, so it is never cleared. A set that outgrows the queue or scans
 //   more than its edge budget is abandoned and deferred.
-// IC, large-set pass: one 512-thread block per deferred set, with an n-bit
+// IC, large-set pass: one 256-thread block per deferred set, with an n-bit
 //   visited bitmap and an n-entry queue. Each batch of up to 256 frontier
 //   vertices is cut into chunks of at most 1024 in-edges that the block's
 //   warps take from a shared counter, so the heavy tail of huge RR sets is
-//   spread over 16 warps. Only __syncthreads barriers are used.
+//   spread over 8 warps. Only __syncthreads barriers are used.
 // LT: the reverse walk of Sec. III-G, one warp per walk: one draw per step,
 //   the chosen in-edge found by a 33-way warp search over the row's sorted
 //   cumulative thresholds, stop at no edge or at a vertex already on the
@@ -73,7 +73,7 @@ __device__ __forceinline__ void decode_item(const SampleLaunch &L, unsigned long
 // batched launches read the instance's row of the descriptor table.
 struct InstView {
   uint32_t n;
-  const uint32_t *off, *src, *thr, *rthr;
+  const uint32_t *off, *src, *thr, *rthr, *rw;
   const uint64_t *cum;
   uint32_t *members;
   unsigned long long store_cap;
@@ -85,7 +85,7 @@ struct InstView {
 };
 
 __device__ __forceinline__ InstView view_of(const InstDesc &d) {
-  return InstView{d.n, d.off, d.src, d.thr, d.rthr, d.cum, d.members, d.store_cap, d.rr_start, d.rr_len, d.cnt,
+  return InstView{d.n, d.off, d.src, d.thr, d.rthr, d.rw, d.cum, d.members, d.store_cap, d.rr_start, d.rr_len, d.cnt,
                   d.key, d.j_begin};
 }
 
@@ -151,12 +151,14 @@ __device__ __forceinline__ uint32_t lim(uint32_t t) { return (t << 8) - 1u; }
 // set iff edge 4grp+qi lies in the row and is live. One Philox call yields
 // the four coin words. The threshold is the row's common one when it has
 // one (rt != kPerEdge; rl = lim(rt)), so the scan of such a row touches no
-// memory.
+// memory; there the usual answer (no live edge: all four words above the
+// bound) is settled by their minimum.
 __device__ __forceinline__ uint32_t group_live(const uint32_t *__restrict__ thr, uint32_t grp, uint32_t s, uint32_t e,
-                                               uint32_t rt, uint32_t rl, uint32_t jlo, uint32_t jhi, PhiloxKey key) {
-  const uint4 r = philox10(grp, kTagEdge, jlo, jhi, key);
+                                               uint32_t rt, uint32_t rl, const CoinKey &ck) {
+  const uint4 r = coin_words(grp, ck);
   uint32_t live;
   if (rt != kPerEdge) {
+    if (min(min(r.x, r.y), min(r.z, r.w)) > rl) return 0u;
     live = (r.x <= rl ? 1u : 0u) | (r.y <= rl ? 2u : 0u) | (r.z <= rl ? 4u : 0u) | (r.w <= rl ? 8u : 0u);
   } else {
     const uint4 tv = reinterpret_cast<const uint4 *>(thr)[grp];
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
     const uint32_t *__restrict__ thr = V.thr;
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
-    const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
+    const CoinKey ck = coin_key((uint32_t)j, (uint32_t)(j >> 32), key);
 
     if (++epoch == 0xFFFFFFFFu) {              // epochs ran out: wipe the table once
       for (uint32_t h = lane; h < kHashSlots; h += 32) ht[h] = 0ull;
@@ -316,8 +318,8 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         for (uint32_t base = g0; base <= g1 && !overflow; base += 64) {   // 64 groups per warp step
           const uint32_t ga = base + lane, gb = base + 32 + lane;
           uint32_t la = 0, lb = 0;
-          if (ga <= g1) la = group_live(thr, ga, s, e, rt, rl, jlo, jhi, key);
-          if (gb <= g1) lb = group_live(thr, gb, s, e, rt, rl, jlo, jhi, key);
+          if (ga <= g1) la = group_live(thr, ga, s, e, rt, rl, ck);
+          if (gb <= g1) lb = group_live(thr, gb, s, e, rt, rl, ck);
           if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
           uint32_t total;
           const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
     const uint32_t *__restrict__ thr = V.thr;
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
-    const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
+    const CoinKey ck = coin_key((uint32_t)j, (uint32_t)(j >> 32), key);
     if (tid == 0) {
       const uint32_t root = draw_root(key, j, V.n);
       q[0] = root;
@@ -453,8 +455,8 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
         for (uint32_t base = c0; base <= c1; base += 64) {   // 64 groups per warp step
           const uint32_t ga = base + lane, gb = base + 32 + lane;
           uint32_t la = 0, lb = 0;
-          if (ga <= c1) la = group_live(thr, ga, s, e, rt, rl, jlo, jhi, key);
-          if (gb <= c1) lb = group_live(thr, gb, s, e, rt, rl, jlo, jhi, key);
+          if (ga <= c1) la = group_live(thr, ga, s, e, rt, rl, ck);
+          if (gb <= c1) lb = group_live(thr, gb, s, e, rt, rl, ck);
           if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
           uint32_t total;
           const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
@@ -533,6 +535,45 @@ __device__ __forceinline__ uint32_t lt_pick(const uint64_t *__restrict__ cum, ui
   return b ? lo + (uint32_t)(__ffs(b) - 1) : hi;
 }
 
+// The in-edge LT chooses at row [s, e) for the draw U: its index, or e for
+// none (the first a with U < cum[a]; Sec. III-G), and in u its source.
+// When every in-edge of the row has the same weight w (rw != kPerEdge) the
+// prefix sums are i·w exactly, so the answer lies within one index of
+// floor(U / (w·2^32)): the warp loads the 32 thresholds and sources around
+// that guess in one round trip and takes the first threshold above U. The
+// window settles the answer unless it starts past s with its first
+// threshold already above U, or ends before e with none above U; then (and
+// for rows of unequal weights) the 33-way search of lt_pick decides.
+__device__ __forceinline__ uint32_t lt_choose(const uint64_t *__restrict__ cum, const uint32_t *__restrict__ src,
+                                              uint32_t s, uint32_t e, uint32_t wbits, uint32_t U, uint32_t &u) {
+  const uint32_t lane = lane_id();
+  if (wbits != kPerEdge) {
+    const uint32_t d = e - s;
+    // fp32 guess (relative error ~2^-22, far inside the window for any row
+    // below 2^20 in-edges; fp64 would run on the GPU's slow double pipe)
+    const float w = __uint_as_float(wbits);
+    float gf = w > 0.0f ? floorf(__uint2float_rn(U) * __frcp_rn(w * 4294967296.0f)) : (float)(d - 1);
+    if (!(gf < (float)(d - 1))) gf = (float)(d - 1);
+    const uint32_t g = gf > 0.0f ? (uint32_t)gf : 0u;
+    const uint32_t w0 = g > 15u ? g - 15u : 0u;                 // window [w0, w0 + 32) within the row
+    const uint32_t p = s + w0 + lane;
+    const bool in = p < e;
+    const bool hit = in && (uint64_t)U < cum[p];
+    const uint32_t sp = in ? src[p] : 0u;
+    const uint32_t b = __ballot_sync(kFullMask, hit);
+    const bool tail = s + w0 + 32u >= e;                       // the window reaches the row's end
+    if (b != 0u && ((b & 1u) == 0u || w0 == 0u)) {
+      const int f = __ffs(b) - 1;
+      u = __shfl_sync(kFullMask, sp, f);
+      return s + w0 + (uint32_t)f;
+    }
+    if (b == 0u && tail) return e;
+  }
+  const uint32_t a = lt_pick(cum, s, e, U);
+  if (a < e) u = src[a];
+  return a;
+}
+
 // kLarge = false keeps the path in shared memory (kLtPathCap per warp) and
 // tests "already visited" by a warp-wide compare against the path; kLarge =
 // true is one warp per block with the slot's bitmap and n-entry queue.
@@ -558,6 +599,7 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     const uint32_t *__restrict__ off = V.off;
     const uint64_t *__restrict__ cum = V.cum;
     const uint32_t *__restrict__ src = V.src;
+    const uint32_t *__restrict__ rw = V.rw;
     const PhiloxKey key = V.key;
     const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
     uint32_t x = draw_root(key, j, V.n);
@@ -569,12 +611,12 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     uint32_t len = 1;
     bool overflow = false;
     for (;;) {
+      const uint32_t s = off[x], e = off[x + 1], wb = rw[x];
       const uint32_t U = philox10(x, kTagStep, jlo, jhi, key).x;
-      const uint32_t s = off[x], e = off[x + 1];
       if (e == s) break;
-      const uint32_t a = lt_pick(cum, s, e, U);
+      uint32_t u = 0;
+      const uint32_t a = lt_choose(cum, src, s, e, wb, U, u);
       if (a >= e) break;
-      const uint32_t u = src[a];
       bool seen;
       if (kLarge) {
         uint32_t old = 0;
@@ -628,15 +670,18 @@ __global__ void uncount_kernel(SampleLaunch L) {
 }
 
 // Pure Philox4x32-10 throughput: each thread draws `per_thread` blocks on
-// consecutive counters (the IC coin counter layout) and folds the words so
-// that nothing is optimised away. Measures the ALU ceiling of the coin work.
+// consecutive counters of one RR set (the IC coin counter layout, computed
+// as the sampler does: coin_key once, coin_words per group) and folds the
+// words so that nothing is optimised away. Measures the ALU ceiling of the
+// coin work.
 __global__ void __launch_bounds__(256) philox_rate_kernel(PhiloxKey key, uint32_t per_thread, uint32_t *sink) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const CoinKey ck = coin_key(0x1234u, 0u, key);
   uint32_t acc = 0;
   for (uint32_t i = 0; i < per_thread; i += 2) {
     const uint32_t c = t * per_thread + i;
-    const uint4 a = philox10(c, kTagEdge, 0x1234u, 0u, key);
-    const uint4 b = philox10(c + 1, kTagEdge, 0x1234u, 0u, key);
+    const uint4 a = coin_words(c, ck);
+    const uint4 b = coin_words(c + 1, ck);
     acc += (a.x ^ a.y ^ a.z ^ a.w) + (b.x ^ b.y ^ b.z ^ b.w);
   }
   if (acc == 0x9E3779B9u) sink[t & 1023] = acc;   // practically never stored

@@ -4,14 +4,18 @@
 // Instead of Alg. 7's scan of the whole RR store for every seed, a
 // vertex -> RR-set inverted index is built once per call (exclusive scan of
 // the occurrence counts, then a fill), so a round only touches the RR sets
-// that contain the new seed. Each round is two kernels:
+// that contain the new seed. Each round has two steps:
 //   argmax: the unselected vertex with the largest count, lowest id on ties
 //           (the max-reduction of Sec. III-H), as a max over 64-bit keys
 //           (count+1) << 32 | ~id; a selected vertex has key ~id < 2^32;
 //   cover:  every RR set containing the seed that is not yet covered is
 //           flagged covered and the counts of its members are lowered.
 // Counts are kept as count + 1 for unselected vertices and 0 once selected.
+// gim_select_seeds runs all k rounds in the persistent greedy kernel
+// (greedy.cu); the allocation-free entry point at the end of this file runs
+// them as two launches per round (argmax_kernel, cover_kernel).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -279,61 +283,6 @@ cudaError_t ensure(T *&p, uint64_t &cap, uint64_t need) {
 }
 
 }  // namespace
-
-cudaError_t run_select(const DevGraph &g, const DevStore &st, uint64_t R, uint64_t Z, uint32_t k, SelectBuffers &b,
-                       int sm_count, cudaStream_t s, uint64_t *launches) {
-  const uint32_t n = g.n;
-  cudaError_t e;
-  // buffers (n-sized ones share one capacity)
-  if (b.n_cap < (uint64_t)n + 1 || !b.cnt_work) {
-    uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap;
-    if ((e = ensure(b.cnt_work, c0, (uint64_t)n + 4)) != cudaSuccess) return e;
-    if ((e = ensure(b.inv_off, c1, (uint64_t)n + 4)) != cudaSuccess) return e;
-    if ((e = ensure(b.cursor, c2, (uint64_t)n + 4)) != cudaSuccess) return e;
-    b.n_cap = std::min(c0, std::min(c1, c2));
-  }
-  if ((e = ensure(b.inv, b.z_cap, std::max<uint64_t>(Z, 1))) != cudaSuccess) return e;
-  if ((e = ensure(b.covered, b.r_cap, std::max<uint64_t>(R, 1))) != cudaSuccess) return e;
-  if (b.k_cap < k || !b.best) {
-    uint64_t c0 = b.k_cap, c1 = b.k_cap, c2 = b.k_cap;
-    if ((e = ensure(b.best, c0, k)) != cudaSuccess) return e;
-    if ((e = ensure(b.seeds, c1, k)) != cudaSuccess) return e;
-    if ((e = ensure(b.gains, c2, k)) != cudaSuccess) return e;
-    b.k_cap = std::min(c0, std::min(c1, c2));
-  }
-  const uint64_t tiles = ((uint64_t)n + kScanTile - 1) / kScanTile;
-  if ((e = ensure(b.scan_tmp, b.scan_cap, tiles + 1)) != cudaSuccess) return e;
-  if (!b.covered_total) {
-    if ((e = cudaMalloc(&b.covered_total, sizeof(unsigned long long))) != cudaSuccess) return e;
-  }
-
-  // inverted index
-  scan_tiles_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(st.cnt, n, b.scan_tmp);
-  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(b.scan_tmp, tiles);
-  scan_apply_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(st.cnt, n, b.scan_tmp, b.inv_off, b.cnt_work, b.cursor);
-  *launches += 3;
-  if (R > 0) {
-    const uint64_t want = (R + 7) / 8;
-    const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)sm_count * 16);
-    fill_inv_kernel<<<blocks, 256, 0, s>>>(st, R, b.inv_off, b.cursor, b.inv);
-    *launches += 1;
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(b.covered, 0, std::max<uint64_t>(R, 1), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(b.best, 0, k * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(b.covered_total, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-
-  const unsigned am_blocks =
-      (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)n / 4 + 255) / 256, (uint64_t)sm_count * 4));
-  const unsigned cv_blocks = (unsigned)sm_count * 8;
-  for (uint32_t t = 0; t < k; ++t) {
-    argmax_kernel<<<am_blocks, 256, 0, s>>>(b.cnt_work, n, b.best + t);
-    cover_kernel<<<cv_blocks, 256, 0, s>>>(t, st, b.best, b.cnt_work, b.inv_off, b.inv, b.covered, b.seeds, b.gains,
-                                           b.covered_total);
-    *launches += 2;
-  }
-  return cudaGetLastError();
-}
 
 }  // namespace gim
 

@@ -1,7 +1,7 @@
 // Autotuner of the sampling schedule (see gim_autotune in gim.h).
 //
 // The knob is the common IC pass's edge budget: how many in-edge groups one
-// warp scans for an RR set before a 512-thread block takes the set over. A
+// warp scans for an RR set before a 256-thread block takes the set over. A
 // small budget sends heavy sets to the block pass early, which bounds the
 // tail of a launch with few sets (one large graph); a large one keeps them
 // on single warps, which is cheaper per coin when many sets are in flight

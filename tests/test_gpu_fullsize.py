@@ -1,0 +1,67 @@
+"""GPU parity at full size, in the launch configuration the benchmark times.
+
+IMM on R-MAT scale 22 (seed 3, weighted-cascade weights 1/indeg(v) in fp32):
+IC with k = 50, eps = 0.1 and LT with k = 100, eps = 0.05, both with
+l = 1 and Philox seed 7, after the same schedule autotuning the benchmark
+runs. The oracle cannot redraw a million RR sets in a test's time, so:
+
+* RR sets: a seeded sample of rr_ids plus the largest sets, each redrawn by
+  the oracle one by one and compared as sorted vertex lists;
+* occurrence counts: equal to the member histogram of the exported store;
+* IMM: the oracle runs Alg. 2 and Alg. 1 over the GPU's collection (each
+  "sample until |R| >= t" served by its first t sets), which must give the
+  same seeds, theta, LB and |R|.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context, binding
+from paper_2009_07325_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2009_07325_gb300 import build
+    build.build()
+    O.build()
+    I.build()
+
+
+@pytest.fixture(scope="module")
+def rmat22_wc():
+    return I.wc_weights(I.rmat(22, 3))
+
+
+def _sampled_sets_match(ctx, orc, model, seed, off, mem, n_sample=256):
+    R = len(off) - 1
+    rng = np.random.default_rng(12345)
+    sizes = np.diff(off)
+    ids = set(rng.choice(R, size=min(n_sample, R), replace=False).tolist())
+    ids |= set(np.argsort(sizes)[-16:].tolist()) | {0, R - 1}
+    for j in sorted(ids):
+        got = np.sort(mem[off[j]:off[j + 1]])
+        want = np.sort(orc.rr_one(model, seed, int(j)))
+        assert np.array_equal(got, want), f"RR set {j} differs"
+    cnt = np.bincount(mem, minlength=ctx.n).astype(np.uint32)
+    assert np.array_equal(ctx.coverage(), cnt)
+
+
+@pytest.mark.parametrize("model,k,eps", [(GIM_IC, 50, 0.1), (GIM_LT, 100, 0.05)])
+def test_imm_rmat22_full_size(rmat22_wc, model, k, eps):
+    g = rmat22_wc
+    ctx = Context(0)
+    ctx.load(g)
+    binding.autotune([ctx], [(model, k, eps, 1.0, 7)], 20000)
+    r = ctx.imm(model, k, eps, 1.0, 7)
+    off, mem = ctx.rr_export()
+    assert len(off) - 1 == r["rr_count"] >= r["theta"]
+    orc = O.Oracle(g)
+    _sampled_sets_match(ctx, orc, model, 7, off, mem)
+    orc.load_csr(off, mem)
+    o = orc.imm_replay(k, eps, 1.0)
+    assert r["seeds"].tolist() == o["seeds"].tolist()
+    assert (r["theta"], r["lb"], r["rr_count"]) == (o["theta"], o["lb"], o["rr_count"])
+    ctx.close()

@@ -164,6 +164,16 @@ def test_store_growth_and_large_sets():
     orc.sample(GIM_IC, 3, 4000, THREADS)
     _same_collection(ctx, orc)
     assert ctx.rr_count()[1] > (1 << 26)
+    # one heavy set in flight at a time (the smallest block-pass scratch): same sets
+    from paper_2009_07325_gb300 import binding
+    one = _ctx(g)
+    one.set_option(binding.GIM_OPT_LARGE_PASS_BYTES, 1)
+    assert one.get_option(binding.GIM_OPT_LARGE_PASS_BYTES) == 1
+    one.sample_rr(GIM_IC, 300, 3)
+    off1, mem1 = one.rr_export()
+    off0, mem0 = orc.export()
+    assert np.array_equal(off1, off0[:301]) and np.array_equal(mem1, mem0[: off0[300]])
+    one.set_option(binding.GIM_OPT_LARGE_PASS_BYTES, 16 << 30)   # back to the default
 
 
 def test_degenerate_weights_and_sizes():
