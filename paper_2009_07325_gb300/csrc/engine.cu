@@ -146,22 +146,26 @@ void shared_release(int device) {
 namespace {
 
 // Large-pass scratch for graphs of up to n vertices (bitmap + n-entry queue per slot).
-gim_status ensure_big(gim_ctx *ctx, DeviceShared &D, uint32_t n) {
+gim_status ensure_big(gim_ctx *ctx, DeviceShared &D, uint32_t n, bool full_queue) {
   const uint64_t budget = ctx->big_budget;
-  if (D.big.slots && D.big.n_cap >= n && D.big_budget == budget) return GIM_OK;
+  const uint32_t qc = full_queue ? n : std::min(n, kSlotQueue);
+  if (D.big.slots && D.big.n_cap >= n && D.big.q_cap >= qc && D.big_budget == budget &&
+      (full_queue || D.big.q_cap <= std::max(qc, kSlotQueue)))
+    return GIM_OK;
   dfree(D.big.bitmap);
   dfree(D.big.queue);
   D.big = BigScratch{};
   const uint64_t words = ((uint64_t)n + 31) / 32;
   const uint64_t wps = (words + 31) / 32 * 32;
-  const uint64_t per = wps * 4 + (uint64_t)n * 4;
+  const uint64_t per = wps * 4 + (uint64_t)qc * 4;
   uint64_t slots = std::min<uint64_t>(budget / std::max<uint64_t>(per, 1), (uint64_t)D.sm_count * 8);
   slots = std::max<uint64_t>(slots, 1);
   CU(cudaMalloc(&D.big.bitmap, wps * 4 * slots));
-  CU(cudaMalloc(&D.big.queue, (uint64_t)n * 4 * slots));
+  CU(cudaMalloc(&D.big.queue, (uint64_t)qc * 4 * slots));
   CU(cudaMemset(D.big.bitmap, 0, wps * 4 * slots));
   D.big.words_per_slot = wps;
   D.big.n_cap = n;
+  D.big.q_cap = qc;
   D.big.slots = (uint32_t)slots;
   D.big_budget = budget;
   return GIM_OK;
@@ -363,7 +367,9 @@ gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s) {
         rollback();
         return set_err(ctx, GIM_ERR_OOM, "large-set pass did not converge");
       }
-      if ((st = ensure_big(ctx, D, nmax)) != GIM_OK) return rollback(), st;
+      // first with capped queues (more sets in flight); what is still pending
+      // after that (a set beyond kSlotQueue members, or a full store) gets n
+      if ((st = ensure_big(ctx, D, nmax, rounds > 1)) != GIM_OK) return rollback(), st;
       Pass Q{true, pending, list_a, list_b};
       if ((st = run_one(ctx, D, model, grp, Q, s, nullptr)) != GIM_OK) return rollback(), st;
       pending = D.h_ctl->n_deferred;

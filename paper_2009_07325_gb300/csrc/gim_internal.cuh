@@ -189,15 +189,18 @@ struct CommonScratch {
 };
 
 // Scratch of the large-set passes: per slot an n-bit visited bitmap (all zero
-// between sets) and an n-entry queue. IC uses one 256-thread block per slot,
+// between sets) and a queue: min(n, kSlotQueue) entries in the first pass,
+// n entries in later ones. IC uses one 256-thread block per slot,
 // LT one warp per slot.
 struct BigScratch {
   uint32_t *bitmap = nullptr;
   uint32_t *queue = nullptr;
   uint64_t words_per_slot = 0;
-  uint32_t n_cap = 0;
+  uint32_t n_cap = 0;                  // vertices the bitmaps cover
+  uint32_t q_cap = 0;                  // queue entries per slot (a set outgrowing them is handed on)
   uint32_t slots = 0;
 };
+constexpr uint32_t kSlotQueue = 1u << 20;   // queue entries per slot in the first large-set pass
 
 constexpr int kBigBlock = 256;
 

@@ -350,8 +350,11 @@ constexpr uint32_t kChunkGroups = 256;       // groups (1024 in-edges) per chunk
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr uint32_t kBigCand = 256;           // per-warp candidate buffer
 
+// Resolves a warp's buffered live edges: a source not yet in the set joins
+// the queue. Past the queue's capacity the vertex is not kept (its bit is
+// cleared again) and the set will be abandoned.
 __device__ __forceinline__ void block_flush(const uint32_t *__restrict__ src, const uint32_t *cand, uint32_t ncand,
-                                            uint32_t *bm, uint32_t *q, uint32_t *s_tail) {
+                                            uint32_t *bm, uint32_t *q, uint32_t qcap, uint32_t *s_tail) {
   const uint32_t lane = lane_id();
   const uint32_t below = (1u << lane) - 1u;
   __syncwarp();
@@ -369,7 +372,13 @@ __device__ __forceinline__ void block_flush(const uint32_t *__restrict__ src, co
       uint32_t base = 0;
       if (lane == 0) base = atomicAdd(s_tail, (uint32_t)__popc(fm));
       base = __shfl_sync(kFullMask, base, 0);
-      if (fresh) q[base + __popc(fm & below)] = u;   // a vertex enters once: the queue holds n
+      if (fresh) {
+        const uint32_t pos = base + __popc(fm & below);
+        if (pos < qcap)
+          q[pos] = u;
+        else
+          atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));
+      }
     }
   }
   __syncwarp();
@@ -385,7 +394,8 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t *cand = cand_all[warp];
   uint32_t *bm = bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot;
-  uint32_t *q = bs.queue + (uint64_t)blockIdx.x * bs.n_cap;
+  const uint32_t qcap = bs.q_cap;
+  uint32_t *q = bs.queue + (uint64_t)blockIdx.x * qcap;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(&L.ctl->next, 1ull);
@@ -412,7 +422,7 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
     uint32_t ncand = 0;                        // this warp's buffered live edges
     for (;;) {
       const uint32_t head = s_head, tail = s_tail;
-      if (head >= tail) break;
+      if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
       const uint32_t nb = tail - head < kBatch ? tail - head : kBatch;
       uint32_t nch = 0;                        // chunks of this thread's frontier vertex
       if (tid < nb) {
@@ -461,7 +471,7 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
           uint32_t total;
           const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
           if (ncand + total > kBigCand) {
-            block_flush(src, cand, ncand, bm, q, &s_tail);
+            block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
             ncand = 0;
           }
           push_live(cand, ncand + excl, ga, la, gb, lb);
@@ -472,15 +482,22 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
       // at least a batch of queued vertices is still unexpanded, the next
       // batch does not need them, and the warps keep them buffered.
       if (tail - (head + nb) < kBatch) {
-        block_flush(src, cand, ncand, bm, q, &s_tail);
+        block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
         ncand = 0;
       }
       __syncthreads();                         // appended vertices visible; batch done
       if (tid == 0) s_head = head + nb;
       __syncthreads();
     }
-    // commit the set: q[0 .. s_tail)
+    // commit the set: q[0 .. s_tail); a set that outgrew the queue is
+    // abandoned (its bits cleared) and handed to a pass with n-entry queues
     const uint32_t size = s_tail;
+    if (size > qcap) {
+      for (uint32_t i = tid; i < qcap; i += kBigBlock) bm[q[i] >> 5] = 0u;
+      if (tid == 0) defer(L, ii, j);
+      __syncthreads();
+      continue;
+    }
     if (tid == 0) s_base = atomicAdd(&L.inst[ii].store_tail, (unsigned long long)size);
     __syncthreads();
     const unsigned long long base = s_base;
@@ -581,9 +598,9 @@ template <bool kLarge>
 __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, BigScratch bs) {
   extern __shared__ uint32_t smem[];
   const uint32_t lane = lane_id();
-  const uint32_t cap = kLarge ? bs.n_cap : kLtPathCap;
+  const uint32_t cap = kLarge ? bs.q_cap : kLtPathCap;
   uint32_t *bm = kLarge ? bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot : nullptr;
-  uint32_t *path = kLarge ? bs.queue + (uint64_t)blockIdx.x * bs.n_cap : smem + (threadIdx.x >> 5) * kLtPathCap;
+  uint32_t *path = kLarge ? bs.queue + (uint64_t)blockIdx.x * bs.q_cap : smem + (threadIdx.x >> 5) * kLtPathCap;
 
   for (;;) {
     unsigned long long item = 0;

@@ -176,6 +176,20 @@ def test_store_growth_and_large_sets():
     one.set_option(binding.GIM_OPT_LARGE_PASS_BYTES, 16 << 30)   # back to the default
 
 
+def test_sets_beyond_the_capped_queue():
+    """p = 1 on ER n = 1.2M: every RR set (~the whole giant component) exceeds the
+    first large-set pass's 2^20-entry queue, is abandoned there and finished by
+    the pass with n-entry queues."""
+    g = I.uniform_weights(I.er(1_200_000, 6_000_000, 8), 1.0)
+    ctx = _ctx(g)
+    orc = O.Oracle(g)
+    ctx.sample_rr(GIM_IC, 12, 5)
+    orc.sample(GIM_IC, 5, 12, THREADS)
+    off, _ = orc.export()
+    assert np.diff(off).min() > (1 << 20)
+    _same_collection(ctx, orc)
+
+
 def test_degenerate_weights_and_sizes():
     base = I.er(300, 1500, 2)
     for p in (0.0, 1.0):
