@@ -45,6 +45,11 @@ WORKLOADS = {
     # R-MAT scale 20, IC weighted cascade, k=50, eps=0.1
     "imm-ic-wc-rmat20": dict(graph=_RMAT.format(s=20, seed=2), weights="weighted cascade 1/indeg(v) fp32",
                              model="IC", k=50, eps=0.1, ell=1.0, philox_seed=7),
+    # the same graph under IC with uniform p = 0.01 (supercritical: ~5% of the RR sets reach a
+    # giant component of ~205K vertices), k = 100. eps = 0.2: at eps = 0.05 the collection
+    # (theta ~1.4e7 sets, ~9.5K members each) would need ~540 GB, beyond the GPU's memory
+    "imm-ic-p001-rmat22": dict(graph=_RMAT.format(s=22, seed=3), weights="uniform p=0.01 fp32",
+                               model="IC", k=100, eps=0.2, ell=1.0, philox_seed=7),
     # directed Erdos-Renyi n=2000, m=20000, IC weighted cascade, k=10, eps=0.5
     "imm-ic-wc-er2000": dict(graph="directed Erdos-Renyi n=2000 m=20000 seed 1",
                              weights="weighted cascade 1/indeg(v) fp32", model="IC", k=10, eps=0.5, ell=1.0,
@@ -361,6 +366,8 @@ class ClockSampler:
 def load_workload():
     from paper_2009_07325_gb300 import inputs as I
     name = WORKLOAD["workload"]
+    if name == "imm-ic-p001-rmat22":
+        return I.uniform_weights(I.rmat(22, 3), 0.01)
     if name.endswith("rmat22"):
         return I.wc_weights(I.rmat(22, 3))
     if name.endswith("rmat20"):
@@ -595,9 +602,11 @@ def run_case(args):
     g = I.uniform_weights(base, 0.01) if args.case == "sample-ic-p001" else I.wc_weights(base)
     model = GIM_LT if args.case == "sample-lt" else GIM_IC
     ctx = Context(0)
+    from paper_2009_07325_gb300 import binding
     if args.large_bytes:
-        from paper_2009_07325_gb300 import binding
         ctx.set_option(binding.GIM_OPT_LARGE_PASS_BYTES, int(args.large_bytes))
+    if args.group_budget:
+        ctx.set_option(binding.GIM_OPT_GROUP_BUDGET, args.group_budget)
     ctx.load(g)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -310,6 +310,13 @@ gim_status gim_rr_count(gim_ctx *ctx, uint64_t *count_out, uint64_t *members_out
  */
 gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out);
 
+/*
+ * Copies RR set rr_id (rr_id < |R|) in ascending vertex order into
+ * members_out (cap entries) and its size into *len_out. A set larger than cap
+ * gives GIM_ERR_ARG with *len_out set, so a caller can retry with room.
+ */
+gim_status gim_rr_get(gim_ctx *ctx, uint64_t rr_id, uint32_t *members_out, uint32_t cap, uint32_t *len_out);
+
 /* Copies the n occurrence counts (RR sets containing each vertex). */
 gim_status gim_coverage_export(gim_ctx *ctx, uint32_t *cnt_out);
 

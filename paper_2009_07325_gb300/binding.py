@@ -71,6 +71,7 @@ SIGNATURES = {
     "gim_last_timings": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_reset_timings": (ctypes.c_int, [_vp]),
     "gim_selection_stats": (ctypes.c_int, [_vp, _c_f64p]),
+    "gim_rr_get": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "gim_diag_philox_rate": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_launch_count": (ctypes.c_int, [_vp, _c_u64p]),
     "gim_last_error_string": (ctypes.c_char_p, [_vp]),
@@ -212,6 +213,20 @@ class Context:
 
     def reset_timings(self):
         self._check(self.L.gim_reset_timings(self.h), "gim_reset_timings")
+
+    def rr_get(self, rr_id: int) -> np.ndarray:
+        """RR set rr_id as an ascending vertex array."""
+        n = ctypes.c_uint32(0)
+        cap = 1024
+        while True:
+            out = np.zeros(cap, np.uint32)
+            st = self.L.gim_rr_get(self.h, int(rr_id), out.ctypes.data, cap, ctypes.byref(n))
+            if st == 0:
+                return out[: n.value].copy()
+            if n.value > cap:
+                cap = int(n.value)
+                continue
+            self._check(st, "gim_rr_get")
 
     def selection_stats(self) -> dict:
         """Selections since reset_timings: device ms, algorithmic bytes, calls, covered-set members."""

@@ -456,6 +456,28 @@ gim_status gim_rr_count(gim_ctx *ctx, uint64_t *count_out, uint64_t *members_out
   return GIM_OK;
 }
 
+gim_status gim_rr_get(gim_ctx *ctx, uint64_t rr_id, uint32_t *members_out, uint32_t cap, uint32_t *len_out) {
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!len_out || (cap > 0 && !members_out)) return set_err(ctx, GIM_ERR_ARG, "null output");
+  if (rr_id >= ctx->R) return set_err(ctx, GIM_ERR_ARG, "rr_id %llu >= |R|", (unsigned long long)rr_id);
+  uint64_t start = 0;
+  uint32_t len = 0;
+  CU(cudaMemcpyAsync(&start, ctx->st.rr_start + rr_id, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(&len, ctx->st.rr_len + rr_id, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (start == kNoStart || start + len > ctx->store_used)
+    return set_err(ctx, GIM_ERR_STATE, "RR set %llu is not stored", (unsigned long long)rr_id);
+  *len_out = len;
+  if (len > cap) return set_err(ctx, GIM_ERR_ARG, "RR set of %u members, room for %u", len, cap);
+  if (len) {
+    CU(cudaMemcpyAsync(members_out, ctx->st.members + start, (uint64_t)len * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::sort(members_out, members_out + len);
+  }
+  return GIM_OK;
+}
+
 gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out) {
   gim_status st = check_ctx(ctx);
   if (st) return st;

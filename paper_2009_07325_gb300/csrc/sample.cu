@@ -189,19 +189,40 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t mine, uint32_t &total) {
   return incl - mine;
 }
 
-// Appends the live edges of one warp step (the lane's groups ga and gb with
-// live masks la and lb) to cand, starting at pos.
-__device__ __forceinline__ void push_live(uint32_t *cand, uint32_t pos, uint32_t ga, uint32_t la, uint32_t gb,
-                                          uint32_t lb) {
+// Groups (of four in-edges) each lane scans per warp step: that many
+// independent Philox chains are in flight per lane.
+constexpr uint32_t kGPL = 2;
+constexpr uint32_t kStepGroups = 32 * kGPL;
+
+// Coins of one warp step over groups [base, base + kStepGroups) of the row
+// [s, e) whose last group is glast; lv[q] holds lane group base + 32q + lane.
+// Returns the lane's number of live edges.
+__device__ __forceinline__ uint32_t step_live(const uint32_t *__restrict__ thr, uint32_t base, uint32_t glast,
+                                              uint32_t s, uint32_t e, uint32_t rt, uint32_t rl, const CoinKey &ck,
+                                              uint32_t (&lv)[kGPL]) {
+  const uint32_t lane = lane_id();
+  uint32_t n = 0;
 #pragma unroll
-  for (int qi = 0; qi < 4; ++qi)
-    if ((la >> qi) & 1u) cand[pos++] = (ga << 2) + qi;
+  for (uint32_t q = 0; q < kGPL; ++q) {
+    const uint32_t g = base + 32 * q + lane;
+    lv[q] = g <= glast ? group_live(thr, g, s, e, rt, rl, ck) : 0u;
+    n += __popc(lv[q]);
+  }
+  return n;
+}
+
+// Appends the live edges of one warp step to cand, starting at pos.
+__device__ __forceinline__ void push_live(uint32_t *cand, uint32_t pos, uint32_t base, const uint32_t (&lv)[kGPL]) {
+  const uint32_t lane = lane_id();
 #pragma unroll
-  for (int qi = 0; qi < 4; ++qi)
-    if ((lb >> qi) & 1u) cand[pos++] = (gb << 2) + qi;
+  for (uint32_t q = 0; q < kGPL; ++q)
+#pragma unroll
+    for (int qi = 0; qi < 4; ++qi)
+      if ((lv[q] >> qi) & 1u) cand[pos++] = ((base + 32 * q + lane) << 2) + qi;
 }
 
 constexpr uint32_t kCandCap = 512;   // per-warp buffer of live edges awaiting their visited test
+static_assert(kCandCap >= 128 * kGPL, "one warp step's live edges fit the buffer");
 
 // Visited set of the common pass: open addressing over kHashSlots 64-bit
 // slots holding epoch << 32 | vertex; a slot whose epoch is not the current
@@ -315,19 +336,17 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         const uint32_t rl = lim(rt);
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
         scanned += g1 - g0 + 1;
-        for (uint32_t base = g0; base <= g1 && !overflow; base += 64) {   // 64 groups per warp step
-          const uint32_t ga = base + lane, gb = base + 32 + lane;
-          uint32_t la = 0, lb = 0;
-          if (ga <= g1) la = group_live(thr, ga, s, e, rt, rl, ck);
-          if (gb <= g1) lb = group_live(thr, gb, s, e, rt, rl, ck);
-          if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
+        for (uint32_t base = g0; base <= g1 && !overflow; base += kStepGroups) {
+          uint32_t lv[kGPL];
+          const uint32_t mine = step_live(thr, base, g1, s, e, rt, rl, ck, lv);
+          if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
           uint32_t total;
-          const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
+          const uint32_t excl = warp_excl(mine, total);
           if (ncand + total > kCandCap) {
             common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
             ncand = 0;
           }
-          push_live(cand, ncand + excl, ga, la, gb, lb);
+          push_live(cand, ncand + excl, base, lv);
           ncand += total;
         }
       }
@@ -348,7 +367,9 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 constexpr uint32_t kBatch = 256;             // frontier vertices per block step
 constexpr uint32_t kChunkGroups = 256;       // groups (1024 in-edges) per chunk
 constexpr uint32_t kBigWarps = kBigBlock / 32;
-constexpr uint32_t kBigCand = 256;           // per-warp candidate buffer
+constexpr int kBigBlocksPerSM = 8;          // register cap that keeps 8 blocks (64 warps) per SM
+constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
+static_assert(kChunkGroups % kStepGroups == 0, "a chunk is whole warp steps");
 
 // Resolves a warp's buffered live edges: a source not yet in the set joins
 // the queue. Past the queue's capacity the vertex is not kept (its bit is
@@ -385,7 +406,7 @@ __device__ __forceinline__ void block_flush(const uint32_t *__restrict__ src, co
 }
 
 template <bool kOne>
-__global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, BigScratch bs, InstDesc one) {
+__global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(SampleLaunch L, BigScratch bs, InstDesc one) {
   __shared__ uint32_t cand_all[kBigWarps][kBigCand];
   __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
   __shared__ uint32_t w_tot[kBigWarps];
@@ -462,19 +483,17 @@ __global__ void __launch_bounds__(kBigBlock) ic_block_kernel(SampleLaunch L, Big
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
         const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkGroups;
         const uint32_t c1 = c0 + kChunkGroups - 1 < g1 ? c0 + kChunkGroups - 1 : g1;
-        for (uint32_t base = c0; base <= c1; base += 64) {   // 64 groups per warp step
-          const uint32_t ga = base + lane, gb = base + 32 + lane;
-          uint32_t la = 0, lb = 0;
-          if (ga <= c1) la = group_live(thr, ga, s, e, rt, rl, ck);
-          if (gb <= c1) lb = group_live(thr, gb, s, e, rt, rl, ck);
-          if (__ballot_sync(kFullMask, (la | lb) != 0u) == 0u) continue;
+        for (uint32_t base = c0; base <= c1; base += kStepGroups) {
+          uint32_t lv[kGPL];
+          const uint32_t mine = step_live(thr, base, c1, s, e, rt, rl, ck, lv);
+          if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
           uint32_t total;
-          const uint32_t excl = warp_excl(__popc(la) + __popc(lb), total);
+          const uint32_t excl = warp_excl(mine, total);
           if (ncand + total > kBigCand) {
             block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
             ncand = 0;
           }
-          push_live(cand, ncand + excl, ga, la, gb, lb);
+          push_live(cand, ncand + excl, base, lv);
           ncand += total;
         }
       }
@@ -668,6 +687,188 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
   }
 }
 
+// LT common pass: four walks per warp, eight lanes each. A walk's step is
+// a chain of dependent loads (the row, then the thresholds around the
+// draw, then the source), so a warp keeps four chains in flight. Each group
+// of eight lanes owns one walk and its path (kLtGroupPath entries in shared
+// memory): the row's window of eight thresholds and sources (or an 9-way
+// search for rows of unequal weights), the visited test against the path
+// eight entries at a time, the commit of the finished path. Every warp-wide
+// primitive runs in code all 32 lanes reach, each group using its own byte of
+// a ballot; a group whose walk ended takes the next work item. Walks longer
+// than the path buffer are handed to the large pass.
+constexpr uint32_t kLtLanes = 8;
+constexpr uint32_t kLtWalks = 32 / kLtLanes;
+constexpr uint32_t kLtGroupPath = 512;
+constexpr uint32_t kLtMultiWarps = 8;   // warps per block
+
+__global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaunch L) {
+  extern __shared__ uint32_t smem[];
+  const uint32_t lane = lane_id();
+  const uint32_t grp = lane / kLtLanes, gl = lane % kLtLanes, lead = grp * kLtLanes;
+  uint32_t *path = smem + ((threadIdx.x >> 5) * kLtWalks + grp) * kLtGroupPath;
+
+  // this group's walk (the same values in all eight lanes)
+  bool active = false, done = false;
+  uint32_t ii = 0, x = 0, len = 0;
+  uint64_t j = 0;
+  InstView V{};
+  for (;;) {
+    // groups without a walk take the next item
+    unsigned long long item = ~0ull;
+    if (!active && !done && gl == 0) item = atomicAdd(&L.ctl->next, 1ull);
+    item = __shfl_sync(kFullMask, item, lead);
+    if (!active && !done) {
+      if (item >= L.total_items) {
+        done = true;
+      } else {
+        decode_item(L, item, ii, j);
+        V = view_of(L.inst[ii]);
+        x = draw_root(V.key, j, V.n);
+        if (gl == 0) path[0] = x;
+        len = 1;
+        active = true;
+      }
+    }
+    __syncwarp();
+    if (__ballot_sync(kFullMask, active) == 0u) break;   // every group is done
+
+    // one step of every active walk
+    bool ended = false, overflow = false;
+    uint32_t u = 0, s = 0, e = 0, wb = kPerEdge, U = 0;
+    if (active) {
+      s = V.off[x];
+      e = V.off[x + 1];
+      wb = V.rw[x];
+      U = philox10(x, kTagStep, (uint32_t)j, (uint32_t)(j >> 32), V.key).x;
+      if (e == s) ended = true;
+    }
+    // window of eight thresholds around the guess (rows of equal weights)
+    bool need = active && !ended;          // still looking for the chosen edge
+    uint32_t w0 = 0;
+    bool use_window = need && wb != kPerEdge;
+    if (use_window) {
+      const uint32_t d = e - s;
+      const float w = __uint_as_float(wb);
+      float gf = w > 0.0f ? floorf(__uint2float_rn(U) * __frcp_rn(w * 4294967296.0f)) : (float)(d - 1);
+      if (!(gf < (float)(d - 1))) gf = (float)(d - 1);
+      const uint32_t g = gf > 0.0f ? (uint32_t)gf : 0u;
+      w0 = g > 3u ? g - 3u : 0u;
+    }
+    {
+      const uint32_t p = s + w0 + gl;
+      const bool in = use_window && p < e;
+      const bool hit = in && (uint64_t)U < V.cum[p];
+      const uint32_t sp = in ? V.src[p] : 0u;
+      const uint32_t b = (__ballot_sync(kFullMask, hit) >> lead) & 0xFFu;
+      const uint32_t f = b ? (uint32_t)(__ffs(b) - 1) : 0u;
+      const uint32_t us = __shfl_sync(kFullMask, sp, lead + f);
+      if (use_window) {
+        if (b != 0u && ((b & 1u) == 0u || w0 == 0u)) {
+          u = us;
+          need = false;
+        } else if (b == 0u && s + w0 + kLtLanes >= e) {
+          ended = true;                     // no edge chosen
+          need = false;
+        }
+      }
+    }
+    // otherwise a 9-way search: the answer lies in [lo, hi], hi = e meaning
+    // no edge; narrowing stops at eight candidates lo..hi, all probed
+    uint32_t lo = s, hi = e;
+    while (__ballot_sync(kFullMask, need) != 0u) {
+      uint32_t p = 0;
+      bool probe = false;
+      if (need) {
+        if (hi - lo >= kLtLanes) {
+          p = lo + (uint32_t)(((uint64_t)(hi - lo) * (gl + 1)) / (kLtLanes + 1));   // < hi
+          probe = true;
+        } else {
+          p = lo + gl;
+          probe = p <= hi && p < e;
+        }
+      }
+      const bool hit = probe && (uint64_t)U < V.cum[p];
+      const uint32_t sp = probe ? V.src[p] : 0u;
+      const uint32_t b = (__ballot_sync(kFullMask, hit) >> lead) & 0xFFu;
+      const uint32_t f = b ? (uint32_t)(__ffs(b) - 1) : 0u;
+      const uint32_t pf = __shfl_sync(kFullMask, p, lead + f);
+      const uint32_t pb = __shfl_sync(kFullMask, p, lead + (f > 0 ? f - 1 : 0));
+      const uint32_t plast = __shfl_sync(kFullMask, p, lead + kLtLanes - 1);
+      const uint32_t us = __shfl_sync(kFullMask, sp, lead + f);
+      if (need) {
+        if (hi - lo >= kLtLanes) {
+          if (b == 0u) {
+            lo = plast + 1;
+          } else {
+            hi = pf;
+            if (f > 0) lo = pb + 1;
+          }
+        } else {
+          // hi < e has a threshold above U, so no hit among lo..hi means hi = e
+          if (b != 0u)
+            u = us;
+          else
+            ended = true;                   // U above every threshold of the row
+          need = false;
+        }
+      }
+    }
+    // visited test against the path, eight entries at a time
+    bool seen = false;
+    {
+      const uint32_t mine = (active && !ended) ? len : 0u;
+      uint32_t top = mine;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(kFullMask, top, o));
+      for (uint32_t i0 = 0; i0 < top; i0 += kLtLanes) {
+        const uint32_t i = i0 + gl;
+        const bool hit = i < mine && path[i] == u;
+        seen |= ((__ballot_sync(kFullMask, hit) >> lead) & 0xFFu) != 0u;
+      }
+    }
+    if (active && !ended) {
+      if (seen) {
+        ended = true;
+      } else if (len == kLtGroupPath) {
+        ended = true;
+        overflow = true;
+      } else {
+        if (gl == 0) path[len] = u;
+        ++len;
+        x = u;
+      }
+    }
+    __syncwarp();
+    // commit the walks that ended
+    const bool commit = active && ended && !overflow;
+    unsigned long long base = 0;
+    if (commit && gl == 0) base = atomicAdd(&L.inst[ii].store_tail, (unsigned long long)len);
+    base = __shfl_sync(kFullMask, base, lead);
+    if (commit) {
+      const bool fits = base + len <= V.store_cap;
+      if (fits)
+        for (uint32_t i = gl; i < len; i += kLtLanes) {
+          const uint32_t m = path[i];
+          V.members[base + i] = m;
+          atomicAdd(&V.cnt[m], 1u);
+        }
+      if (gl == 0) {
+        if (fits) {
+          V.rr_start[j] = base;
+          V.rr_len[j] = len;
+          atomicAdd(&L.inst[ii].members_added, (unsigned long long)len);
+        } else {
+          defer(L, ii, j);
+        }
+      }
+    }
+    if (active && overflow && gl == 0) defer(L, ii, j);
+    if (active && ended) active = false;
+    __syncwarp();
+  }
+}
+
 // Rollback helper: lowers the occurrence counts of the sets of a launch's
 // items that were stored (rr_start != kNoStart).
 __global__ void uncount_kernel(SampleLaunch L) {
@@ -714,8 +915,14 @@ int ic_common_blocks_per_sm() {
 
 int lt_common_blocks_per_sm() {
   int b = 0;
-  const size_t sm = 8 * kLtPathCap * sizeof(uint32_t);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lt_kernel<false>, 256, sm) != cudaSuccess) b = 4;
+  const size_t sm = kLtMultiWarps * kLtWalks * kLtGroupPath * sizeof(uint32_t);
+  // more than 48 KB of dynamic shared memory must be allowed (per device)
+  if (cudaFuncSetAttribute(lt_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    cudaGetLastError();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lt_multi_kernel, 32 * kLtMultiWarps, sm) != cudaSuccess) {
+    cudaGetLastError();
+    b = 2;
+  }
   return b > 0 ? b : 1;
 }
 
@@ -737,7 +944,7 @@ cudaError_t launch_ic_block(const SampleLaunch &L, const BigScratch &bs, uint32_
 }
 
 cudaError_t launch_lt_common(const SampleLaunch &L, uint32_t grid, cudaStream_t s) {
-  lt_kernel<false><<<grid, 256, 8 * kLtPathCap * sizeof(uint32_t), s>>>(L, BigScratch{});
+  lt_multi_kernel<<<grid, 32 * kLtMultiWarps, kLtMultiWarps * kLtWalks * kLtGroupPath * sizeof(uint32_t), s>>>(L);
   return cudaGetLastError();
 }
 

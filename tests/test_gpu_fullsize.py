@@ -65,3 +65,34 @@ def test_imm_rmat22_full_size(rmat22_wc, model, k, eps):
     assert r["seeds"].tolist() == o["seeds"].tolist()
     assert (r["theta"], r["lb"], r["rr_count"]) == (o["theta"], o["lb"], o["rr_count"])
     ctx.close()
+
+
+def test_imm_rmat22_ic_p001_full_size():
+    """IC with uniform p = 0.01 on R-MAT-22, k = 100, eps = 0.2 (about 10^10 members:
+    too many to export or replay), checked on sampled RR sets and through
+    properties that hold at any size."""
+    g = I.uniform_weights(I.rmat(22, 3), 0.01)
+    k, eps = 100, 0.2
+    ctx = Context(0)
+    ctx.load(g)
+    binding.autotune([ctx], [(GIM_IC, k, eps, 1.0, 7)], 5000)
+    r = ctx.imm(GIM_IC, k, eps, 1.0, 7)
+    R, Z = ctx.rr_count()
+    assert R == r["rr_count"] >= r["theta"]
+    # theta from the oracle's constants and the LB the run found
+    c = O.imm_constants(g.n, k, eps, 1.0)
+    assert r["lb"] >= 1.0 and r["theta"] == int(np.ceil(c["lambda_star"] / r["lb"]))
+    # sampled RR sets, redrawn by the oracle one by one
+    orc = O.Oracle(g)
+    rng = np.random.default_rng(99)
+    for j in sorted(set(rng.choice(R, 48, replace=False).tolist()) | {0, R - 1}):
+        assert np.array_equal(ctx.rr_get(j), np.sort(orc.rr_one(GIM_IC, 7, j))), f"RR set {j} differs"
+    # counts sum to the store; the first seed is the lowest-id argmax of the counts
+    cnt = ctx.coverage().astype(np.int64)
+    assert int(cnt.sum()) == Z
+    s, gains, cov = ctx.select_seeds(k)
+    assert s.tolist() == r["seeds"].tolist()
+    assert s[0] == int(np.argmax(cnt)) and gains[0] == cnt.max()
+    assert len(set(s.tolist())) == k and all(a >= b for a, b in zip(gains[:-1], gains[1:]))
+    assert int(gains.astype(np.int64).sum()) == cov <= R
+    ctx.close()
