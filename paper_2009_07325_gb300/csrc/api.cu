@@ -37,7 +37,9 @@ void free_graph(DevGraph &g) {
   g = DevGraph{};
 }
 
-void free_select(SelectBuffers &b) {
+}  // namespace
+
+void gim::free_select_buffers(SelectBuffers &b) {
   dfree(b.cnt_work);
   dfree(b.inv_off);
   dfree(b.cursor);
@@ -54,6 +56,10 @@ void free_select(SelectBuffers &b) {
   dfree(b.hmeta);
   b = SelectBuffers{};
 }
+
+namespace {
+
+void free_select(SelectBuffers &b) { free_select_buffers(b); }
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -36,7 +36,8 @@ constexpr uint32_t kTileItems = kTile / kSelThreads;
 struct SelDesc {
   uint32_t n, k, active, count_own;       // count_own: cnt is computed here from sets [0, R)
   unsigned long long R;
-  unsigned long long set_begin;           // prefix of R over the batch (fill kernel)
+  unsigned long long fill_R;              // sets this instance adds to the index (0 when ext)
+  unsigned long long set_begin;           // prefix of fill_R over the batch (fill kernel)
   unsigned long long count_from;          // count_own: sets [0, count_from) are already in cnt
   unsigned long long cnt_begin;           // prefix of the sets counted this round (count kernel)
   const uint32_t *members;
@@ -54,6 +55,8 @@ struct SelDesc {
   uint32_t *hbits;                        // hub rows of `words` words
   uint32_t *hmeta;                        // hub count, ids, counts + 1
   unsigned int *err;                      // bit 1: more hubs than kHeavyCap (cannot happen: see hub_min)
+  uint32_t ext;                           // 1: lists, hub split and rows come from another instance's index
+  const uint32_t *ext_hmeta;              // that index's hub count and ids
   unsigned long long *best;               // k argmax keys
   uint32_t *seeds;                        // k (into the batch's packed seeds)
   uint32_t *gains;                        // k (packed)
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_count(const SelDesc *d, uint
 __global__ void __launch_bounds__(kSelThreads) bsel_tile_sums(const SelDesc *d, uint32_t ni) {
   const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
   const SelDesc &D = d[i];
-  if (!D.active) return;
+  if (!D.active || D.ext) return;
   const uint64_t base = (uint64_t)(blockIdx.x - D.tile_begin) * kTile + (uint64_t)threadIdx.x * kTileItems;
   unsigned long long s = 0;
   for (uint32_t t = 0; t < kTileItems; ++t)
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_sums(const SelDesc *d, 
 __global__ void __launch_bounds__(kSelThreads) bsel_tile_scan(const SelDesc *d, uint32_t ni) {
   for (uint32_t i = blockIdx.x; i < ni; i += gridDim.x) {
     const SelDesc &D = d[i];
-    if (!D.active) continue;
+    if (!D.active || D.ext) continue;
     unsigned long long carry = 0;
     for (uint32_t b = 0; b < D.tiles; b += kSelThreads) {
       const uint32_t t = b + threadIdx.x;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_scan(const SelDesc *d, 
 __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint32_t ni) {
   const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
   const SelDesc &D = d[i];
-  if (!D.active) return;
+  if (!D.active || D.ext) return;
   const uint32_t tile = blockIdx.x - D.tile_begin;
   const uint64_t base = (uint64_t)tile * kTile + (uint64_t)threadIdx.x * kTileItems;
   uint32_t v[kTileItems];
@@ -245,11 +248,33 @@ __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint
   }
 }
 
+// An instance on another instance's index: the light counts from its own
+// counts with that index's hub split, its hub counts for that index's hubs
+// (blockIdx.y: instance).
+__global__ void __launch_bounds__(kSelThreads) bsel_ext_apply(const SelDesc *d, uint32_t ni) {
+  for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
+    const SelDesc &D = d[i];
+    if (!D.active || !D.ext) continue;
+    const uint32_t H = D.ext_hmeta[0] < kHeavyCap ? D.ext_hmeta[0] : kHeavyCap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < D.n; x += stride)
+      D.cnt_work[x] = D.hslot[x] == 0xFFu ? D.cnt[x] + 1u : 0u;
+    if (blockIdx.x == 0) {
+      for (uint32_t t = threadIdx.x; t < H; t += blockDim.x) {
+        const uint32_t v = D.ext_hmeta[1 + t];
+        D.hmeta[1 + t] = v;
+        D.hmeta[1 + kHeavyCap + t] = D.cnt[v] + 1u;
+      }
+      if (threadIdx.x == 0) D.hmeta[0] = H;
+    }
+  }
+}
+
 // Zeroes the bitmap rows of the hubs found (blockIdx.y: instance).
 __global__ void __launch_bounds__(kSelThreads) bsel_hub_clear(const SelDesc *d, uint32_t ni) {
   for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
     const SelDesc &D = d[i];
-    if (!D.active) continue;
+    if (!D.active || D.ext) continue;
     const uint32_t H = D.hmeta[0] < kHeavyCap ? D.hmeta[0] : kHeavyCap;
     const uint64_t total = (uint64_t)H * D.words;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -261,7 +286,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_hub_clear(const SelDesc *d, 
 // each light member and set in the bitmap row of each hub member (one warp
 // per set).
 __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint32_t ni) {
-  const unsigned long long total = d[ni - 1].set_begin + d[ni - 1].R;   // this round's sets over the batch
+  const unsigned long long total = d[ni - 1].set_begin + d[ni - 1].fill_R;   // this round's sets over the batch
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -332,6 +357,7 @@ cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uin
   bsel_tile_sums<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
   bsel_tile_scan<<<ni, kSelThreads, 0, s>>>(d, ni);
   bsel_apply<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_ext_apply<<<dim3(64, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_hub_clear<<<dim3(128, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_fill<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
   return cudaGetLastError();
@@ -417,7 +443,8 @@ struct MultiSelect::Impl {
 MultiSelect::MultiSelect() : p(new Impl) {}
 MultiSelect::~MultiSelect() { delete p; }
 
-gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k) {
+gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k,
+                                  const std::vector<bool> *index_only) {
   Impl &B = *p;
   B.ni = (uint32_t)n.size();
   B.h.assign(B.ni, SelDesc{});
@@ -434,7 +461,7 @@ gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, 
     tiles += D.tiles;
     B.seed_off[i + 1] = B.seed_off[i] + D.k;
     nmax = std::max(nmax, D.n);
-    nsum += D.n;
+    if (!(index_only && (*index_only)[i])) nsum += D.n;
   }
   B.scan_blocks = tiles;
   B.fill_blocks = (uint32_t)ctx->sm_count * 8;
@@ -450,7 +477,8 @@ gim_status MultiSelect::configure(gim_ctx *ctx, const std::vector<uint32_t> &n, 
   uint32_t cur = 0;
   for (uint32_t i = 0; i < B.ni; ++i) {
     GreedyDesc &g = B.gh[i];
-    const double share = nsum > 0 ? (double)G * n[i] / nsum : 1.0;
+    const bool only = index_only && (*index_only)[i];
+    const double share = (nsum > 0 && !only) ? (double)G * n[i] / nsum : 1.0;
     uint32_t nb = (uint32_t)std::max(1.0, std::floor(share));
     nb = std::min<uint32_t>(nb, std::max<uint32_t>(1, (n[i] + 8191) / 8192));
     nb = std::min(nb, G);
@@ -493,10 +521,12 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     D.set_begin = total_sets;
     D.cnt_begin = total_counted;
     D.R = D.active ? x.R : 0;
+    D.ext = (D.active && x.index) ? 1u : 0u;
+    D.fill_R = D.ext ? 0 : D.R;
     D.count_own = 0;
     D.count_from = 0;
     if (!D.active) continue;
-    total_sets += x.R;
+    total_sets += D.fill_R;
     SelectBuffers &b = *x.buf;
     const uint32_t *own_before = b.cnt_own;
     if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || !b.hslot ||
@@ -517,9 +547,11 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     D.words = (uint32_t)((x.R + 31) / 32);
     const uint64_t hm = std::max<uint64_t>(std::max<uint64_t>((x.R + 31) / 32, (x.Z + kHeavyCap - 1) / kHeavyCap), 1);
     D.hub_min = (uint32_t)std::min<uint64_t>(hm, 0xFFFFFFFFull);
-    CU(ensure_buf(b.inv, b.z_cap, std::max<uint64_t>(x.Z, 1)));
+    if (!D.ext) {
+      CU(ensure_buf(b.inv, b.z_cap, std::max<uint64_t>(x.Z, 1)));
+      CU(ensure_buf(b.hbits, b.hb_cap, (uint64_t)kHeavyCap * std::max<uint32_t>(D.words, 1)));
+    }
     CU(ensure_buf(b.covered, b.r_cap, std::max<uint64_t>(D.words, 1)));
-    CU(ensure_buf(b.hbits, b.hb_cap, (uint64_t)kHeavyCap * std::max<uint32_t>(D.words, 1)));
     if (!b.hmeta) CU(cudaMalloc(&b.hmeta, (1 + 2 * kHeavyCap) * sizeof(uint32_t)));
     if (b.k_cap < D.k || !b.best || !b.seeds || !b.gains) {   // the three k-sized buffers share k_cap
       uint64_t k0 = b.k_cap, k1 = b.k_cap, k2 = b.k_cap;
@@ -556,13 +588,30 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     D.hbits = b.hbits;
     D.hmeta = b.hmeta;
     D.err = B.sync + B.ni;
+    D.ext_hmeta = nullptr;
+  }
+  // lists, hub split and rows of the shared indexes: taken only now, once
+  // every instance (the index builders among them) has its buffers
+  for (uint32_t i = 0; i < B.ni; ++i) {
+    SelDesc &D = B.h[i];
+    if (!D.ext) continue;
+    const SelectBuffers &ix = *in[i].index;
+    if (!ix.inv_off || !ix.inv || !ix.hslot || !ix.hbits || !ix.hmeta || ix.n_cap < (uint64_t)D.n + 4)
+      return set_err(ctx, GIM_ERR_STATE, "selection: a shared index without its buffers");
+    D.inv_off = ix.inv_off;
+    D.inv = ix.inv;
+    D.hslot = ix.hslot;
+    D.hbits = ix.hbits;
+    D.ext_hmeta = ix.hmeta;
   }
   for (uint32_t i = 0; i < B.ni; ++i) {
     const SelDesc &D = B.h[i];
     GreedyDesc &g = B.gh[i];
-    g.k = D.active ? D.k : 0u;
+    g.k = D.active && !in[i].index_only ? D.k : 0u;
     if (!D.active) continue;
     g.words = D.words;
+    g.row_words = D.ext ? (uint32_t)((in[i].index_R + 31) / 32) : D.words;
+    g.R = (uint32_t)D.R;
     g.cnt_work = D.cnt_work;
     g.inv_off = D.inv_off;
     g.inv = D.inv;
@@ -596,7 +645,7 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
   }
   CU(cudaEventRecord(ctx->ev[8], s));
   CU(cudaGraphLaunch(B.exec, s));
-  ctx->launches += 8;
+  ctx->launches += 9;
   for (size_t w = 0; w < B.wave_first.size(); ++w) {
     const uint32_t first = B.wave_first[w];
     const uint32_t count = (w + 1 < B.wave_first.size() ? B.wave_first[w + 1] : B.ni) - first;
@@ -629,8 +678,8 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     const SelDesc &D = B.h[i];
     if (!D.active) continue;
     const double n = D.n, Z = (double)in[i].Z;
-    ctx->sel_bytes += 8.0 * Z + 4.0 * n + (double)D.k * 4.0 * n + 4.0 * (double)B.h_stats[2 * i + 1] +
-                      12.0 * (double)B.h_stats[2 * i] + 4.0 * D.words;
+    ctx->sel_bytes += (D.ext ? 0.0 : 8.0 * Z) + 4.0 * n + (double)D.k * 4.0 * n +
+                      4.0 * (double)B.h_stats[2 * i + 1] + 12.0 * (double)B.h_stats[2 * i] + 4.0 * D.words;
     ctx->sel_cov_members += (double)B.h_stats[2 * i];
   }
   return GIM_OK;

@@ -245,12 +245,17 @@ struct SelectBuffers {
   uint64_t n_cap = 0, z_cap = 0, r_cap = 0, k_cap = 0, scan_cap = 0, hb_cap = 0;
 };
 
+// Frees every buffer of b and resets it (api.cu).
+void free_select_buffers(SelectBuffers &b);
+
 // The k greedy rounds of one instance in the persistent greedy kernel
 // (greedy.cu). Blocks [g_begin, g_begin + g_blocks) of the launch serve it.
 struct GreedyDesc {
   uint32_t n = 0, k = 0;                 // k = 0: nothing to select
   uint32_t g_begin = 0, g_blocks = 0;
-  uint32_t words = 0;                    // ceil(R/32): covered bitmap words, hub row length
+  uint32_t words = 0;                    // ceil(R/32): covered bitmap words, hub row words read
+  uint32_t row_words = 0;                // hub row stride (the index's own ceil(R/32))
+  uint32_t R = 0;                        // sets selected over: list entries >= R are skipped
   uint32_t *cnt_work = nullptr;          // n: light count + 1 while unselected, else 0
   const uint64_t *inv_off = nullptr;     // n + 1 (hubs have empty lists)
   const uint32_t *inv = nullptr;         // rr ids per light vertex
@@ -347,6 +352,13 @@ struct SelInput {
   uint64_t count_from = 0;               // cnt == null: buf->cnt_own already counts sets [0, count_from)
   SelectBuffers *buf = nullptr;          // the instance's selection buffers (grown on demand)
   uint32_t k = 0;                        // rounds this time (<= the configured k); 0: the configured k
+  // Optional: use the index (inverted lists, hub split, hub rows) that
+  // another instance of the same run builds or built over a collection this
+  // one is a prefix of (the server's pools); its lists and rows are read up
+  // to set R only. index_R = the sets that index covers.
+  const SelectBuffers *index = nullptr;
+  uint64_t index_R = 0;
+  bool index_only = false;               // build this instance's index only (no greedy rounds)
 };
 
 // Greedy selection of a fixed set of slots (n, k fixed), one CUDA graph per
@@ -355,7 +367,9 @@ class MultiSelect {
  public:
   MultiSelect();
   ~MultiSelect();
-  gim_status configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k);
+  // index_only (optional): instances that only ever build an index get one greedy block
+  gim_status configure(gim_ctx *ctx, const std::vector<uint32_t> &n, const std::vector<uint32_t> &k,
+                       const std::vector<bool> *index_only = nullptr);
   // Runs one selection round of every active slot; cov, seeds (and gains)
   // come back packed by slot (seed_offset).
   gim_status run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaStream_t s, std::vector<unsigned long long> &cov,

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc
       const uint64_t i0 = D.inv_off[u], i1 = D.inv_off[u + 1];
       for (uint64_t p = i0 + gwarp; p < i1; p += nwarps) {
         const uint32_t j = D.inv[p];
+        if (j >= D.R) continue;   // beyond this instance's prefix of a shared index
         uint32_t fresh = 0;
         if (lane == 0) {
           const uint32_t bit = 1u << (j & 31u);
@@ -219,12 +220,13 @@ __global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc
     } else {
       // hub seed: its bitmap row, 32 words per warp; the warp then covers the
       // new sets of those words one at a time
-      const uint32_t *row = D.hbits + (uint64_t)us * D.words;
+      const uint32_t *row = D.hbits + (uint64_t)us * D.row_words;
+      const uint32_t last_mask = (D.R & 31u) ? (1u << (D.R & 31u)) - 1u : 0xFFFFFFFFu;
       for (uint32_t w0 = gwarp * 32u; w0 < D.words; w0 += nwarps * 32u) {
         const uint32_t w = w0 + lane;
         uint32_t mine = 0;
         if (w < D.words) {
-          const uint32_t bits = row[w] & ~__ldcg(D.covered + w);
+          const uint32_t bits = row[w] & ~__ldcg(D.covered + w) & (w + 1 == D.words ? last_mask : 0xFFFFFFFFu);
           if (bits) mine = bits & ~atomicOr(D.covered + w, bits);
         }
         newly += __popc(mine);

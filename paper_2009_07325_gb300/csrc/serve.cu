@@ -64,6 +64,11 @@ struct gim_server {
   std::map<std::pair<int, uint64_t>, gim_ctx *> pools;   // (model, seed) -> RR pool sharing the graph
   std::vector<SelectBuffers> slot_buf;
   std::vector<Query *> slot_q;
+  // shared indexes: instance max_active + i of ms builds the index of pool
+  // index_pool[i] over its first index_R[i] sets
+  std::vector<SelectBuffers> index_buf;
+  std::vector<gim_ctx *> index_pool;
+  std::vector<uint64_t> index_R;
   MultiSelect ms;
   std::deque<Query *> waiting;
   std::map<uint64_t, std::unique_ptr<Query>> all;
@@ -172,8 +177,43 @@ gim_status round_once(gim_server *S, std::vector<Query *> &active) {
     return st;
   }
   const auto t1 = Clock::now();
-  // 2. every admitted query's greedy selection over its own prefix
-  std::vector<SelInput> in(S->max_active);
+  // 2. every admitted query's greedy selection over its own prefix. A pool
+  // with room among the shared indexes gets one index over all its sets,
+  // rebuilt only when the pool has grown; a query whose prefix is at least a
+  // quarter of its pool uses it (its lists read up to the prefix) instead of
+  // indexing its prefix itself
+  const uint32_t ni = (uint32_t)S->index_buf.size();
+  std::vector<SelInput> in(S->max_active + ni);
+  std::map<gim_ctx *, int> pool_index;
+  for (Query *q : active) {
+    if (pool_index.count(q->pool)) continue;
+    int ix = -1;
+    for (uint32_t i = 0; i < ni; ++i)
+      if (S->index_pool[i] == q->pool) ix = (int)i;
+    for (uint32_t i = 0; i < ni && ix < 0; ++i) {
+      bool used = false;   // a free entry: its pool has no admitted query now
+      for (Query *o : active) used |= S->index_pool[i] == o->pool;
+      if (!used) {
+        ix = (int)i;
+        S->index_pool[i] = q->pool;
+        S->index_R[i] = 0;
+      }
+    }
+    pool_index[q->pool] = ix;
+    if (ix >= 0 && S->index_R[ix] != q->pool->R) {
+      SelInput &x = in[S->max_active + ix];
+      x.active = true;
+      x.index_only = true;
+      x.R = q->pool->R;
+      x.Z = q->pool->Z;
+      x.members = q->pool->st.members;
+      x.rr_start = q->pool->st.rr_start;
+      x.rr_len = q->pool->st.rr_len;
+      x.cnt = q->pool->st.cnt;   // the pool's occurrence counts over all its sets
+      x.k = 1;
+      x.buf = &S->index_buf[ix];
+    }
+  }
   for (Query *q : active) {
     SelInput &x = in[q->slot];
     x.active = true;
@@ -186,10 +226,17 @@ gim_status round_once(gim_server *S, std::vector<Query *> &active) {
     x.count_from = q->counted;
     x.k = q->p.k;
     x.buf = &S->slot_buf[q->slot];
+    const int ix = pool_index[q->pool];
+    if (ix >= 0 && 4 * q->Rq >= q->pool->R) {
+      x.index = &S->index_buf[ix];
+      x.index_R = q->pool->R;
+    }
   }
   std::vector<unsigned long long> cov;
   std::vector<uint32_t> seeds;
   if ((st = S->ms.run(S->self, in, S->stream, cov, seeds)) != GIM_OK) return st;
+  for (auto &kv : pool_index)
+    if (kv.second >= 0) S->index_R[kv.second] = kv.first->R;
   const auto t2 = Clock::now();
   S->sample_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
   S->select_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
@@ -313,13 +360,22 @@ gim_status gim_server_start(gim_server **out, gim_ctx *graph_ctx, uint32_t max_a
   S->budget = mem_budget_bytes ? mem_budget_bytes : (uint64_t)(0.6 * (double)free_b);
   S->slot_buf.resize(max_active);
   S->slot_q.assign(max_active, nullptr);
+  constexpr uint32_t kSharedIndexes = 4;
+  S->index_buf.resize(kSharedIndexes);
+  S->index_pool.assign(kSharedIndexes, nullptr);
+  S->index_R.assign(kSharedIndexes, 0);
   gim_status st = make_view(S.get(), &S->self);
   if (st != GIM_OK) {
     cudaStreamDestroy(S->stream);
     return set_err(graph_ctx, st, "server context");
   }
-  std::vector<uint32_t> ns(max_active, graph_ctx->g.n), ks(max_active, max_k);
-  st = S->ms.configure(S->self, ns, ks);
+  std::vector<uint32_t> ns(max_active + S->index_buf.size(), graph_ctx->g.n), ks(ns.size(), max_k);
+  std::vector<bool> only(ns.size(), false);
+  for (size_t i = max_active; i < ks.size(); ++i) {   // index-only instances
+    ks[i] = 1;
+    only[i] = true;
+  }
+  st = S->ms.configure(S->self, ns, ks, &only);
   if (st != GIM_OK) {
     graph_ctx->last_error = S->self->last_error;
     gim_destroy(S->self);
@@ -404,18 +460,8 @@ void gim_server_stop(gim_server *S) {
   cudaStreamSynchronize(S->stream);
   for (auto &kv : S->pools) gim_destroy(kv.second);
   gim_destroy(S->self);
-  for (SelectBuffers &b : S->slot_buf) {
-    cudaFree(b.cnt_work);
-    cudaFree(b.inv_off);
-    cudaFree(b.cursor);
-    cudaFree(b.inv);
-    cudaFree(b.covered);
-    cudaFree(b.best);
-    cudaFree(b.seeds);
-    cudaFree(b.gains);
-    cudaFree(b.scan_tmp);
-    cudaFree(b.cnt_own);
-  }
+  for (SelectBuffers &b : S->slot_buf) free_select_buffers(b);
+  for (SelectBuffers &b : S->index_buf) free_select_buffers(b);
   cudaStreamDestroy(S->stream);
   delete S;
 }
