@@ -23,11 +23,12 @@
 //   epoch, so it is never cleared. A set that outgrows the queue or scans
 //   more than its edge budget is abandoned and deferred.
 // IC, large-set pass: one 256-thread block per deferred set, with an n-bit
-//   visited bitmap and an n-entry queue. Each batch of up to 256 frontier
-//   vertices is cut into chunks of at most 1024 in-edges that the block's
+//   visited bitmap and a queue. Each batch of up to 512 frontier
+//   vertices is cut into chunks of at most 2048 in-edges that the block's
 //   warps take from a shared counter, so the heavy tail of huge RR sets is
 //   spread over 8 warps. Only __syncthreads barriers are used.
-// LT: the reverse walk of Sec. III-G, one warp per walk: one draw per step,
+// LT: the reverse walk of Sec. III-G (four walks per warp in the common pass, see
+//   lt_multi_kernel; one warp per walk in the large pass): one draw per step,
 //   the chosen in-edge found by a 33-way warp search over the row's sorted
 //   cumulative thresholds, stop at no edge or at a vertex already on the
 //   path (common pass: path in shared memory; large pass: queue + bitmap).
@@ -364,8 +365,9 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 // ---------------------------------------------------------------------------
 // IC large-set pass: one block of kBigBlock threads per RR set.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kBatch = 256;             // frontier vertices per block step
-constexpr uint32_t kChunkGroups = 256;       // groups (1024 in-edges) per chunk
+constexpr uint32_t kRowsPerThread = 2;       // frontier rows each thread loads per block step
+constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step
+constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr int kBigBlocksPerSM = 8;          // register cap that keeps 8 blocks (64 warps) per SM
 constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
@@ -445,25 +447,40 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       const uint32_t head = s_head, tail = s_tail;
       if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
       const uint32_t nb = tail - head < kBatch ? tail - head : kBatch;
-      uint32_t nch = 0;                        // chunks of this thread's frontier vertex
-      if (tid < nb) {
-        const uint32_t v = q[head + tid];
-        const uint32_t s = off[v], e = off[v + 1], rt = rthr[v];
-        b_s[tid] = s;
-        b_e[tid] = e;
-        b_rt[tid] = rt;
-        nch = (e > s && rt != 0u) ? (((e - 1) >> 2) - (s >> 2) + kChunkGroups) / kChunkGroups : 0u;
+      uint32_t nch[kRowsPerThread], mine = 0;  // chunks of this thread's frontier rows
+#pragma unroll
+      for (uint32_t r = 0; r < kRowsPerThread; ++r) {
+        const uint32_t b = tid * kRowsPerThread + r;
+        nch[r] = 0;
+        if (b < nb) {
+          const uint32_t v = q[head + b];
+          const uint32_t s = off[v], e = off[v + 1], rt = rthr[v];
+          b_s[b] = s;
+          b_e[b] = e;
+          b_rt[b] = rt;
+          nch[r] = (e > s && rt != 0u) ? (((e - 1) >> 2) - (s >> 2) + kChunkGroups) / kChunkGroups : 0u;
+        }
+        mine += nch[r];
       }
-      // block-wide exclusive prefix of the chunk counts (threads >= kBatch hold 0)
+      // block-wide exclusive prefix of the chunk counts (rows >= nb hold 0)
       uint32_t wsum;
-      const uint32_t wex = warp_excl(nch, wsum);
+      const uint32_t wex = warp_excl(mine, wsum);
       if (lane == 0) w_tot[warp] = wsum;
       if (tid == 0) s_next = 0;
       __syncthreads();
-      uint32_t before = 0;
-      for (uint32_t w = 0; w < warp; ++w) before += w_tot[w];
-      if (tid < nb) b_pre[tid] = before + wex;
-      if (tid == nb - 1) b_pre[nb] = before + wex + nch;
+      uint32_t before = 0, all = 0;
+      for (uint32_t w = 0; w < kBigWarps; ++w) {
+        if (w < warp) before += w_tot[w];
+        all += w_tot[w];
+      }
+      uint32_t run = before + wex;
+#pragma unroll
+      for (uint32_t r = 0; r < kRowsPerThread; ++r) {
+        const uint32_t b = tid * kRowsPerThread + r;
+        if (b < nb) b_pre[b] = run;
+        run += nch[r];
+      }
+      if (tid == 0) b_pre[nb] = all;
       __syncthreads();
       const uint32_t nchunks = b_pre[nb];
       for (;;) {
