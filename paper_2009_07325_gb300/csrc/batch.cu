@@ -46,7 +46,7 @@ struct SelDesc {
   uint32_t *cnt;                          // occurrence counts (written by bsel_count when count_own)
   uint32_t *cnt_work;
   uint64_t *inv_off;
-  uint32_t *cursor;
+  unsigned long long *cursor;
   uint32_t *inv;
   uint32_t *covered;                      // words of the covered bitmap
   uint32_t words;                         // ceil(R/32)
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_scan(const SelDesc *d, 
 // Splits the vertices: a hub (count >= hub_min) takes the next hub slot,
 // with its id and count + 1 in hmeta; a light vertex keeps count + 1 in
 // cnt_work and gets its inverted list's offset (exclusive scan of the light
-// counts) and a zero cursor.
+// counts) and a cursor at that offset.
 __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint32_t ni) {
   const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
   const SelDesc &D = d[i];
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint
     const bool hub = v[t] >= D.hub_min;
     if (x < D.n) {
       D.inv_off[x] = run;
-      D.cursor[x] = 0u;
+      D.cursor[x] = run;
       uint8_t hs = 0xFFu;
       uint32_t cw = v[t] + 1u;
       if (hub) {
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint3
     // four members per lane in flight: the cursor atomics return a value, so
     // the loop is bound by their latency
     for (uint32_t t0 = 0; t0 < len; t0 += 128) {
-      uint32_t x[4], hs[4], c[4];
-      uint64_t o[4];
+      uint32_t x[4], hs[4];
+      unsigned long long pos[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint32_t t = t0 + 32 * q + lane;
@@ -312,16 +312,14 @@ __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint3
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (x[q] == 0xFFFFFFFFu) continue;
-        if (hs[q] != 0xFFu) {
+        if (hs[q] != 0xFFu)
           atomicOr(D.hbits + (uint64_t)hs[q] * D.words + (j >> 5), 1u << (j & 31u));
-        } else {
-          c[q] = atomicAdd(&D.cursor[x[q]], 1u);
-          o[q] = D.inv_off[x[q]];
-        }
+        else
+          pos[q] = atomicAdd(&D.cursor[x[q]], 1ull);   // the entry's place in inv, in one round trip
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (x[q] != 0xFFFFFFFFu && hs[q] == 0xFFu) D.inv[o[q] + c[q]] = (uint32_t)j;
+        if (x[q] != 0xFFFFFFFFu && hs[q] == 0xFFu) D.inv[pos[q]] = (uint32_t)j;
     }
   }
 }

@@ -230,7 +230,7 @@ constexpr uint32_t kHeavyCap = 255;     // hubs per selection at most (slot ids 
 struct SelectBuffers {
   uint32_t *cnt_work = nullptr;  // n: light count + 1 while unselected, 0 once selected or a hub
   uint64_t *inv_off = nullptr;   // n+1
-  uint32_t *cursor = nullptr;    // n
+  unsigned long long *cursor = nullptr;   // n: the next free position of each light vertex's list in inv
   uint32_t *inv = nullptr;       // Z rr ids
   uint32_t *covered = nullptr;   // ceil(R/32) words: bit j set once RR set j is covered
   unsigned long long *best = nullptr;   // k argmax keys

@@ -91,7 +91,7 @@ namespace {
 uint64_t pool_bytes(gim_ctx *c) { return c->st.cap * 4 + c->rr_cap * 12 + (uint64_t)c->g.n * 4; }
 
 uint64_t slot_bytes(const SelectBuffers &b) {
-  return b.n_cap * 24 + b.z_cap * 4 + b.r_cap + b.k_cap * 16 + b.scan_cap * 8;
+  return b.n_cap * 29 + b.z_cap * 4 + b.r_cap * 4 + b.k_cap * 16 + b.scan_cap * 8;
 }
 
 // Projected device bytes a query adds: its share of pool growth plus its
