@@ -90,6 +90,9 @@ def _lib_():
             L.orc_imm.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_uint64, ctypes.c_int, u32p, u64p, f64p, f64p]
             L.orc_imm.restype = ctypes.c_int
+            L.orc_imm_fresh.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_uint64, ctypes.c_int, u32p, u64p, f64p, f64p]
+            L.orc_imm_fresh.restype = ctypes.c_int
             L.orc_imm_replay.argtypes = [vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, u32p, u64p, f64p,
                                          f64p]
             L.orc_imm_replay.restype = ctypes.c_int
@@ -192,6 +195,19 @@ class Oracle:
         mem = np.ascontiguousarray(members, np.uint32) if len(members) else np.zeros(1, np.uint32)
         if self.L.orc_load_collection(self.h, len(off) - 1, off, mem) != 0:
             raise ValueError("bad collection")
+
+    def imm_fresh(self, model: int, k: int, eps: float, ell: float, seed: int, threads: int = 1):
+        """IMM whose final greedy runs over theta fresh RR sets (rr_ids 2^63 + j)."""
+        seeds = np.zeros(k, np.uint32)
+        theta = np.zeros(1, np.uint64)
+        lb = np.zeros(1, np.float64)
+        trace = np.zeros(4 * 64, np.float64)
+        rc = self.L.orc_imm_fresh(self.h, model, k, eps, ell, seed, threads, seeds, theta, lb, trace)
+        if rc < 0:
+            raise RuntimeError(f"oracle fresh imm failed ({rc})")
+        tr = trace[: 4 * min(rc, 64)].reshape(-1, 4)
+        rounds = [dict(x=r[0], theta_i=int(r[1]), covered=int(r[2]), rr_count=int(r[3])) for r in tr]
+        return dict(seeds=seeds, theta=int(theta[0]), lb=float(lb[0]), rounds=rounds, rr_count=self.rr_count)
 
     def imm_replay(self, k: int, eps: float, ell: float):
         """IMM (Alg. 2 then Alg. 1) with every sampling step served by a prefix of

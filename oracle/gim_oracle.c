@@ -108,6 +108,7 @@ typedef struct orc {
   int model;           /* -1 while empty */
   uint64_t seed;
   uint64_t count;      /* |R| */
+  uint64_t ctr_base;   /* RR set at position j is drawn with rr_id ctr_base + j (0 except in a fresh final phase) */
   uint64_t cap_sets, cap_members;
   uint64_t *rr_off;    /* count+1 */
   uint32_t *members;   /* rr_off[count] */
@@ -293,7 +294,8 @@ int orc_sample(orc *g, int model, uint64_t seed, uint64_t count, int threads) {
     c->sizes = (uint32_t *)malloc((b - a) * sizeof(uint32_t) + 4);
     if (!visited || !out || !c->mem || !c->sizes) { fail = 1; }
     for (uint64_t j = a; j < b && !fail; ++j) {
-      uint32_t s = model == 0 ? rr_ic(g, seed, j, visited, out) : rr_lt(g, seed, j, visited, out);
+      const uint64_t id = g->ctr_base + j;
+      uint32_t s = model == 0 ? rr_ic(g, seed, id, visited, out) : rr_lt(g, seed, id, visited, out);
       if (c->n_members + s > c->cap) {
         uint64_t nc = c->cap;
         while (nc < c->n_members + s) nc *= 2;
@@ -465,7 +467,8 @@ static int grow_to(orc *g, int model, uint64_t seed, int threads, uint64_t avail
 }
 
 static int imm_core(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed, int threads,
-                    uint64_t avail, uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
+                    uint64_t avail, int fresh, uint32_t *seeds, uint64_t *theta_out, double *lb_out,
+                    double *trace) {
   double c[5];
   orc_imm_constants(g->n, k, eps, ell, c);
   const double epsp = c[1], lam_prime = c[2], lam_star = c[3];
@@ -493,8 +496,19 @@ static int imm_core(orc *g, int model, uint32_t k, double eps, double ell, uint6
     }
   }
   const uint64_t theta = (uint64_t)ceil(lam_star / LB);
-  int rc = grow_to(g, model, seed, threads, avail, theta);
-  if (rc) return rc;
+  if (fresh) {
+    /* the final phase on theta new RR sets, drawn with rr_ids 2^63 + j, independent of the
+       sets the lower-bound search used */
+    g->count = 0;
+    g->rr_off[0] = 0;
+    g->ctr_base = 1ull << 63;
+    int rc = orc_sample(g, model, seed, theta, threads);
+    g->ctr_base = 0;
+    if (rc) return rc;
+  } else {
+    int rc = grow_to(g, model, seed, threads, avail, theta);
+    if (rc) return rc;
+  }
   if (orc_greedy(g, k, seeds, NULL) < 0) return -2;
   if (theta_out) *theta_out = theta;
   if (lb_out) *lb_out = LB;
@@ -505,7 +519,22 @@ int orc_imm(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed
             uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
   if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
   if (g->count != 0) return -1;
-  return imm_core(g, model, k, eps, ell, seed, threads, 0, seeds, theta_out, lb_out, trace);
+  return imm_core(g, model, k, eps, ell, seed, threads, 0, 0, seeds, theta_out, lb_out, trace);
+}
+
+/*
+ * IMM with a fresh final phase: the lower-bound search of orc_imm, then theta
+ * new RR sets (rr_ids 2^63, 2^63 + 1, ..., independent of the search's sets)
+ * replace the collection and the greedy runs over them. This is the variant
+ * that avoids reusing the search's sets in the final estimate (a later
+ * correction to IMM's analysis; the paper runs IMM as published). Afterwards
+ * |R| = theta.
+ */
+int orc_imm_fresh(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed, int threads,
+                  uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
+  if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
+  if (g->count != 0) return -1;
+  return imm_core(g, model, k, eps, ell, seed, threads, 0, 1, seeds, theta_out, lb_out, trace);
 }
 
 /*
@@ -522,7 +551,7 @@ int orc_imm_replay(orc *g, uint32_t k, double eps, double ell, uint32_t *seeds, 
   const uint64_t avail = g->count;
   if (!avail) return -1;
   g->count = 0;
-  const int rc = imm_core(g, 0, k, eps, ell, 0, 1, avail, seeds, theta_out, lb_out, trace);
+  const int rc = imm_core(g, 0, k, eps, ell, 0, 1, avail, 0, seeds, theta_out, lb_out, trace);
   if (rc < 0) g->count = avail;
   return rc;
 }

@@ -140,3 +140,48 @@ def test_imm_replay_equals_fresh_imm(oracle_mod, inputs_mod, model):
     short.load_csr(off[: fresh["rr_count"]], mem[: int(off[fresh["rr_count"] - 1])])
     with pytest.raises(RuntimeError):
         short.imm_replay(10, 0.5, 1.0)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_imm_fresh_final_phase(oracle_mod, inputs_mod, model):
+    """IMM with a fresh final phase: the lower-bound search is IMM's own, and the
+    final greedy runs over exactly theta new RR sets whose rr_ids are 2^63 + j."""
+    g = inputs_mod.wc_weights(inputs_mod.er(2000, 20000, 1))
+    mdl = oracle_mod.IC if model == "ic" else oracle_mod.LT
+    base = oracle_mod.Oracle(g).imm(mdl, 10, 0.5, 1.0, 7)
+    o = oracle_mod.Oracle(g)
+    fr = o.imm_fresh(mdl, 10, 0.5, 1.0, 7)
+    assert fr["rounds"] == base["rounds"]
+    assert (fr["theta"], fr["lb"]) == (base["theta"], base["lb"])
+    assert fr["rr_count"] == fr["theta"]
+    off, mem = o.export()
+    for j in list(range(0, 40)) + list(range(fr["theta"] - 40, fr["theta"])):
+        want = sorted(o.rr_one(mdl, 7, (1 << 63) + j).tolist())
+        assert sorted(mem[int(off[j]):int(off[j + 1])].tolist()) == want
+    # rr_id 2^63 + j is not rr_id j: the collection is not the search's
+    same = sum(sorted(o.rr_one(mdl, 7, j).tolist()) == sorted(o.rr_one(mdl, 7, (1 << 63) + j).tolist())
+               for j in range(200))
+    assert same < 200
+    # the greedy over the fresh sets, rerun from a copy of them, picks the same seeds
+    chk = oracle_mod.Oracle(g)
+    chk.load_csr(off, mem)
+    assert chk.greedy(10)[0].tolist() == fr["seeds"].tolist()
+
+
+@pytest.mark.parametrize("model,gseed", [("ic", 51), ("lt", 53)])
+def test_imm_fresh_quality_against_exact_opt(oracle_mod, inputs_mod, model, gseed):
+    """The fresh variant's seeds also reach (1 - 1/e - eps) OPT, with exact spreads."""
+    if model == "ic":
+        g = inputs_mod.tiny_graph(7, 13, gseed)
+        _, R, prob = exact_ic(g)
+        mdl = oracle_mod.IC
+    else:
+        g = inputs_mod.tiny_graph(7, 12, gseed, weights="lt", max_indeg_sum=1.0)
+        _, R, prob = exact_lt(g)
+        mdl = oracle_mod.LT
+    k, eps = 2, 0.3
+    opt = max(spread(R, prob, S) for S in itertools.combinations(range(g.n), k))
+    for s in range(4):
+        res = oracle_mod.Oracle(g).imm_fresh(mdl, k, eps, 1.0, 200 + s)
+        assert spread(R, prob, res["seeds"].tolist()) >= (1 - math.exp(-1) - eps) * opt
+        assert len(set(res["seeds"].tolist())) == k
