@@ -358,6 +358,16 @@ gim_status gim_selection_stats(gim_ctx *ctx, double out[4]);
  */
 gim_status gim_diag_philox_rate(gim_ctx *ctx, double *calls_per_s);
 
+/*
+ * Diagnostic of the failure path of the greedy selection's bounded waits (the
+ * paper has no counterpart): runs the persistent greedy kernel on a tiny
+ * instance whose block group is declared as two blocks while only one is
+ * launched, so its group barrier can never be met. The wait gives up after
+ * about 2 s; the call then returns GIM_ERR_TIMEOUT and *waited_ms (nullable)
+ * holds the kernel's time. No fault is raised and the context stays usable.
+ */
+gim_status gim_diag_barrier_timeout(gim_ctx *ctx, double *waited_ms);
+
 /* Number of kernels this context has launched since it was created. */
 gim_status gim_launch_count(gim_ctx *ctx, uint64_t *out);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "gim_selection_stats": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_rr_get": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "gim_diag_philox_rate": (ctypes.c_int, [_vp, _c_f64p]),
+    "gim_diag_barrier_timeout": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_launch_count": (ctypes.c_int, [_vp, _c_u64p]),
     "gim_last_error_string": (ctypes.c_char_p, [_vp]),
     "gim_select_seeds_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp,
@@ -233,6 +234,13 @@ class Context:
         out = np.zeros(4, np.float64)
         self._check(self.L.gim_selection_stats(self.h, _p(out, _c_f64p)), "gim_selection_stats")
         return dict(kernel_ms=out[0], bytes=out[1], calls=int(out[2]), covered_members=out[3])
+
+    def diag_barrier_timeout(self):
+        """Runs the greedy kernel with a barrier that can never be met; returns
+        (status, ms): GIM_ERR_TIMEOUT (4) and the time the bounded wait took."""
+        out = ctypes.c_double(0)
+        st = self.L.gim_diag_barrier_timeout(self.h, ctypes.byref(out))
+        return int(st), float(out.value)
 
     def philox_rate(self) -> float:
         """Measured Philox4x32-10 calls per second of this device (ALU ceiling of the coins)."""

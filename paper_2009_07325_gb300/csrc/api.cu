@@ -551,6 +551,61 @@ gim_status gim_selection_stats(gim_ctx *ctx, double out[4]) {
   return GIM_OK;
 }
 
+gim_status gim_diag_barrier_timeout(gim_ctx *ctx, double *waited_ms) {
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  // one allocation carved into the tiny instance's buffers (n = 4, k = 1)
+  constexpr size_t kBytes = 4096;
+  unsigned char *buf = nullptr;
+  CU(cudaMalloc(&buf, kBytes));
+  CU(cudaMemsetAsync(buf, 0, kBytes, ctx->stream));
+  const uint32_t cw_init[4] = {2u, 5u, 3u, 1u};
+  CU(cudaMemcpyAsync(buf, cw_init, sizeof cw_init, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemsetAsync(buf + 512, 0xFF, 4, ctx->stream));   // hslot: all light
+  GreedyDesc d;
+  d.n = 4;
+  d.k = 1;
+  d.g_begin = 0;
+  d.g_blocks = 2;   // declared two, launched one: the barrier is never met
+  d.words = 1;
+  d.row_words = 1;
+  d.R = 0;
+  d.cnt_work = reinterpret_cast<uint32_t *>(buf);
+  d.inv_off = reinterpret_cast<const uint64_t *>(buf + 64);
+  d.inv = reinterpret_cast<const uint32_t *>(buf + 128);
+  d.covered = reinterpret_cast<uint32_t *>(buf + 192);
+  d.hslot = reinterpret_cast<const uint8_t *>(buf + 512);
+  d.hbits = reinterpret_cast<const uint32_t *>(buf + 576);
+  d.hmeta = reinterpret_cast<uint32_t *>(buf + 1024);   // hub count 0
+  d.members = reinterpret_cast<const uint32_t *>(buf + 640);
+  d.rr_start = reinterpret_cast<const uint64_t *>(buf + 704);
+  d.rr_len = reinterpret_cast<const uint32_t *>(buf + 768);
+  d.best = reinterpret_cast<unsigned long long *>(buf + 832);
+  d.seeds = reinterpret_cast<uint32_t *>(buf + 896);
+  d.gains = reinterpret_cast<uint32_t *>(buf + 928);
+  d.covered_total = reinterpret_cast<unsigned long long *>(buf + 960);
+  d.stats = reinterpret_cast<unsigned long long *>(buf + 976);
+  d.bar = reinterpret_cast<unsigned int *>(buf + 3072);
+  unsigned int *err = reinterpret_cast<unsigned int *>(buf + 3136);
+  GreedyDesc *dd = reinterpret_cast<GreedyDesc *>(buf + 3200);
+  static_assert(sizeof(GreedyDesc) <= 4096 - 3200, "descriptor fits");
+  CU(cudaMemcpyAsync(dd, &d, sizeof d, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaEventRecord(ctx->ev[6], ctx->stream));
+  cudaError_t e = launch_greedy(dd, 1, 1, err, ctx->stream);
+  CU(cudaEventRecord(ctx->ev[7], ctx->stream));
+  unsigned int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof flag, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  float ms = 0;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "barrier timeout diagnostic");
+  if (waited_ms) *waited_ms = ms;
+  ctx->launches++;
+  if (flag) return set_err(ctx, GIM_ERR_TIMEOUT, "greedy selection: a block barrier wait gave up (diagnostic)");
+  return set_err(ctx, GIM_ERR_STATE, "barrier timeout diagnostic: the wait did not give up");
+}
+
 gim_status gim_diag_philox_rate(gim_ctx *ctx, double *calls_per_s) {
   gim_status st = check_ctx(ctx);
   if (st) return st;
