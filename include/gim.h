@@ -262,7 +262,9 @@ gim_status gim_server_poll(gim_server *srv, uint64_t ticket, uint32_t timeout_ms
 gim_status gim_server_stats(gim_server *srv, double out[8]);
 void gim_server_stop(gim_server *srv);
 
-/* Tuning knobs of a context (they change speed, never results). */
+/* Options of a context. GIM_OPT_GROUP_BUDGET and GIM_OPT_LARGE_PASS_BYTES
+   are tuning knobs: they change speed, never results. GIM_OPT_FRESH_FINAL
+   selects a variant of IMM and changes its results. */
 typedef enum {
   /* In-edge groups (4 in-edges each) one RR set may scan in the warp-per-set
      IC pass before it is handed to the block-per-set pass. Default 16384. */
@@ -272,10 +274,22 @@ typedef enum {
      shared by its contexts). Heavy sets in flight = min(bytes / (n/8 + 4n),
      8 x SM count), at least 1. Default 16 GiB; lower it to leave room for
      other work on the GPU. */
-  GIM_OPT_LARGE_PASS_BYTES = 1
+  GIM_OPT_LARGE_PASS_BYTES = 1,
+  /* 1: gim_imm and gim_batch_imm run IMM's final phase on fresh RR sets.
+     After the lower-bound search (Alg. 2) the collection is emptied and
+     theta new sets are drawn with rr_ids 2^63, 2^63 + 1, ... (Philox
+     counter words j_lo = j, j_hi = 2^31), stored at positions 0 .. theta-1;
+     the greedy (Alg. 1) runs over them, so the final estimate does not
+     reuse the sets the search selected on. The paper reuses them (IMM as
+     published); this is the later correction of IMM's analysis. theta and
+     LB are unchanged; rr_count = theta. The collection keeps its counter
+     base until it is reset. The server always runs IMM as published.
+     0 (default): reuse. Values other than 0 and 1 are rejected. */
+  GIM_OPT_FRESH_FINAL = 2
 } gim_option;
 
-/* Sets a tuning knob. Errors: GIM_ERR_ARG (unknown option or value 0). */
+/* Sets an option. Errors: GIM_ERR_ARG (unknown option, value 0 for the
+   tuning knobs, value above 1 for GIM_OPT_FRESH_FINAL). */
 gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value);
 
 /* Reads a tuning knob into *value. */

@@ -341,12 +341,13 @@ int orc_load_collection(orc *g, uint64_t count, const uint64_t *offsets, const u
   memcpy(g->rr_off, offsets, (count + 1) * sizeof(uint64_t));
   memcpy(g->members, members, offsets[count] * sizeof(uint32_t));
   g->count = count;
+  g->ctr_base = 0;
   g->model = -2;
   g->seed = 0;
   return 0;
 }
 
-void orc_reset(orc *g) { g->count = 0; g->rr_off[0] = 0; g->model = -1; }
+void orc_reset(orc *g) { g->count = 0; g->rr_off[0] = 0; g->model = -1; g->ctr_base = 0; }
 uint64_t orc_rr_count(const orc *g) { return g->count; }
 uint64_t orc_store_size(const orc *g) { return g->rr_off[g->count]; }
 
@@ -501,9 +502,8 @@ static int imm_core(orc *g, int model, uint32_t k, double eps, double ell, uint6
        sets the lower-bound search used */
     g->count = 0;
     g->rr_off[0] = 0;
-    g->ctr_base = 1ull << 63;
+    g->ctr_base = 1ull << 63;   /* kept: the collection left in place is that stream's prefix */
     int rc = orc_sample(g, model, seed, theta, threads);
-    g->ctr_base = 0;
     if (rc) return rc;
   } else {
     int rc = grow_to(g, model, seed, threads, avail, theta);

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgim.so")
 GIM_IC, GIM_LT = 0, 1
 GIM_OPT_GROUP_BUDGET = 0
 GIM_OPT_LARGE_PASS_BYTES = 1
+GIM_OPT_FRESH_FINAL = 2
 STATUS = {0: "GIM_OK", 1: "GIM_ERR_ARG", 2: "GIM_ERR_OOM", 3: "GIM_ERR_CUDA", 4: "GIM_ERR_TIMEOUT",
           5: "GIM_ERR_STATE"}
 

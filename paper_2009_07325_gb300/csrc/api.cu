@@ -248,6 +248,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   free_select(ctx->sel);
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
+  ctx->jhi = 0;
   CU(cudaMalloc(&ctx->st.cnt, (uint64_t)n * 4 + 16));
   CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)n * 4 + 16, s));
   CU(cudaStreamSynchronize(s));
@@ -296,6 +297,7 @@ gim_status gim_reset_rr(gim_ctx *ctx) {
   if (!ctx->has_graph) return GIM_OK;
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
+  ctx->jhi = 0;
   CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)ctx->g.n * 4, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return GIM_OK;
@@ -377,6 +379,10 @@ gim_status gim_imm(gim_ctx *ctx, gim_model model, uint32_t k, double eps, double
     }
   }
   const uint64_t theta = (uint64_t)std::ceil(c.lam2 / LB);
+  if (ctx->fresh_final) {   // theta new sets, rr_ids 2^63 + j, replace the search's collection
+    if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
+    ctx->jhi = 1u << 31;
+  }
   if ((st = sample_to(theta)) != GIM_OK) return st;
   if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, nullptr, nullptr); })) != GIM_OK) return st;
   if (theta_out) *theta_out = theta;
@@ -423,7 +429,11 @@ gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value) {
     ctx->big_budget = value;
     return GIM_OK;
   }
-  return set_err(ctx, GIM_ERR_ARG, "unknown option or zero value");
+  if (opt == GIM_OPT_FRESH_FINAL && value <= 1) {
+    ctx->fresh_final = value == 1;
+    return GIM_OK;
+  }
+  return set_err(ctx, GIM_ERR_ARG, "unknown option or value out of range");
 }
 
 gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value) {
@@ -434,6 +444,10 @@ gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value) {
   }
   if (opt == GIM_OPT_LARGE_PASS_BYTES) {
     *value = ctx->big_budget;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_FRESH_FINAL) {
+    *value = ctx->fresh_final ? 1 : 0;
     return GIM_OK;
   }
   return set_err(ctx, GIM_ERR_ARG, "unknown option");

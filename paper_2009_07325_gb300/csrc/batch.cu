@@ -695,6 +695,7 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
     gim_ctx *c = ctxs[i];
     c->R = c->Z = c->store_used = 0;
     c->model = -1;
+    c->jhi = 0;
     CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
     imm_init(S[i], c->g.n, params[i]);
     ns[i] = c->g.n;
@@ -715,6 +716,11 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
       if (S[i].phase == 2) continue;
       any = true;
       gim_ctx *c = ctxs[i];
+      if (S[i].phase == 1 && c->fresh_final && c->jhi == 0) {   // fresh final phase: rr_ids 2^63 + j
+        c->R = c->Z = c->store_used = 0;
+        c->jhi = 1u << 31;
+        CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
+      }
       const uint64_t target = imm_target(S[i], c->g.n);
       if (target >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "instance %u: theta above 2^32-2 RR sets", i);
       if (target > c->R) jobs.push_back(SampleJobH{c, (int)params[i].model, params[i].seed, target - c->R});

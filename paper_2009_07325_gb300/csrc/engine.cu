@@ -226,6 +226,7 @@ void fill_desc(InstDesc &d, gim_ctx *c, uint64_t seed, uint64_t item_begin) {
   d.cnt = c->st.cnt;
   d.key = PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
   d.j_begin = c->R;
+  d.jhi = c->jhi;
   d.item_begin = item_begin;
   d.store_tail = c->store_used;
   d.members_added = 0;

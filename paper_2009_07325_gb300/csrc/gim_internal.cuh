@@ -97,9 +97,10 @@ __host__ __device__ __forceinline__ uint4 coin_words(uint32_t g, const CoinKey &
   return make_uint4(c0, c1, c2, c3);
 }
 
-// randSelect(V) of Alg. 3: the root of RR set j, high word of a 64-bit draw times n.
-__device__ __forceinline__ uint32_t draw_root(PhiloxKey key, uint64_t j, uint32_t n) {
-  const uint4 r = philox10(0u, kTagRoot, (uint32_t)j, (uint32_t)(j >> 32), key);
+// randSelect(V) of Alg. 3: the root of the RR set with rr_id (jhi:jlo), high
+// word of a 64-bit draw times n.
+__device__ __forceinline__ uint32_t draw_root(PhiloxKey key, uint32_t jlo, uint32_t jhi, uint32_t n) {
+  const uint4 r = philox10(0u, kTagRoot, jlo, jhi, key);
   const uint64_t w = ((uint64_t)r.y << 32) | r.x;
   return (uint32_t)__umul64hi(w, (uint64_t)n);
 }
@@ -135,7 +136,7 @@ struct DevStore {
 struct InstDesc {
   // graph
   uint32_t n;
-  uint32_t pad0;
+  uint32_t jhi;   // high word of every rr_id of this job: 0, or 2^31 for a fresh final phase (rr_ids 2^63 + j)
   const uint32_t *off, *src, *thr, *rthr, *rw;
   const uint64_t *cum;
   // RR collection
@@ -413,6 +414,7 @@ struct gim_ctx {
   // RR collection
   int model = -1;
   uint64_t seed = 0;
+  uint32_t jhi = 0;   // rr_id of the set at position j is (jhi:j): 2^31 after a fresh final phase, else 0
   uint64_t R = 0;                 // |R|
   uint64_t Z = 0;                 // members over all stored sets
   uint64_t store_used = 0;        // store entries reserved (>= Z: holes after a store overflow)
@@ -422,6 +424,7 @@ struct gim_ctx {
   bool shared_held = false;       // holds a reference on the device's shared scratch
   uint32_t group_budget = 1u << 14;   // GIM_OPT_GROUP_BUDGET
   uint64_t big_budget = 16ull << 30;  // GIM_OPT_LARGE_PASS_BYTES
+  bool fresh_final = false;           // GIM_OPT_FRESH_FINAL
 
   gim::SelectBuffers sel;
   gim::MultiSelect *msel = nullptr;   // gim_select_seeds / gim_imm: a one-slot batched selection

@@ -83,11 +83,12 @@ struct InstView {
   uint32_t *cnt;
   PhiloxKey key;
   unsigned long long j_begin;
+  uint32_t jhi;   // the rr_id of the set at position j is (jhi:j); positions stay below 2^32
 };
 
 __device__ __forceinline__ InstView view_of(const InstDesc &d) {
   return InstView{d.n, d.off, d.src, d.thr, d.rthr, d.rw, d.cum, d.members, d.store_cap, d.rr_start, d.rr_len, d.cnt,
-                  d.key, d.j_begin};
+                  d.key, d.j_begin, d.jhi};
 }
 
 // Instance and rr_id of work item `item`, and the instance's view.
@@ -300,14 +301,14 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
     const uint32_t *__restrict__ thr = V.thr;
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
-    const CoinKey ck = coin_key((uint32_t)j, (uint32_t)(j >> 32), key);
+    const CoinKey ck = coin_key((uint32_t)j, V.jhi, key);
 
     if (++epoch == 0xFFFFFFFFu) {              // epochs ran out: wipe the table once
       for (uint32_t h = lane; h < kHashSlots; h += 32) ht[h] = 0ull;
       __syncwarp();
       epoch = 1;
     }
-    const uint32_t root = draw_root(key, j, V.n);
+    const uint32_t root = draw_root(key, (uint32_t)j, V.jhi, V.n);
     if (lane == 0) {
       q[0] = root;
       ht[(root * 0x9E3779B1u) >> (32 - kHashBits)] = ((unsigned long long)epoch << 32) | root;
@@ -433,9 +434,9 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
     const uint32_t *__restrict__ thr = V.thr;
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
-    const CoinKey ck = coin_key((uint32_t)j, (uint32_t)(j >> 32), key);
+    const CoinKey ck = coin_key((uint32_t)j, V.jhi, key);
     if (tid == 0) {
-      const uint32_t root = draw_root(key, j, V.n);
+      const uint32_t root = draw_root(key, (uint32_t)j, V.jhi, V.n);
       q[0] = root;
       bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
       s_head = 0;
@@ -654,8 +655,8 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     const uint32_t *__restrict__ src = V.src;
     const uint32_t *__restrict__ rw = V.rw;
     const PhiloxKey key = V.key;
-    const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)(j >> 32);
-    uint32_t x = draw_root(key, j, V.n);
+    const uint32_t jlo = (uint32_t)j, jhi = V.jhi;
+    uint32_t x = draw_root(key, (uint32_t)j, V.jhi, V.n);
     if (lane == 0) {
       path[0] = x;
       if (kLarge) bm[x >> 5] = 1u << (x & 31u);
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
       } else {
         decode_item(L, item, ii, j);
         V = view_of(L.inst[ii]);
-        x = draw_root(V.key, j, V.n);
+        x = draw_root(V.key, (uint32_t)j, V.jhi, V.n);
         if (gl == 0) path[0] = x;
         len = 1;
         active = true;
@@ -757,7 +758,7 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
       s = V.off[x];
       e = V.off[x + 1];
       wb = V.rw[x];
-      U = philox10(x, kTagStep, (uint32_t)j, (uint32_t)(j >> 32), V.key).x;
+      U = philox10(x, kTagStep, (uint32_t)j, V.jhi, V.key).x;
       if (e == s) ended = true;
     }
     // window of eight thresholds around the guess (rows of equal weights)
