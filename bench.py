@@ -54,7 +54,16 @@ WORKLOADS = {
     "imm-ic-wc-er2000": dict(graph="directed Erdos-Renyi n=2000 m=20000 seed 1",
                              weights="weighted cascade 1/indeg(v) fp32", model="IC", k=10, eps=0.5, ell=1.0,
                              philox_seed=7),
+    # the headline with IMM's final phase on theta fresh RR sets (rr_ids 2^63 + j)
+    "imm-ic-wc-rmat22-fresh": dict(graph=_RMAT.format(s=22, seed=3), weights="weighted cascade 1/indeg(v) fp32",
+                                   model="IC", k=50, eps=0.1, ell=1.0, philox_seed=7, fresh_final=True),
 }
+# Barabasi-Albert density sweep (Sec. IV-F): n = 10^6, r = 2 .. 32 undirected edges per new vertex
+# (both directions stored), clique of r0 = r vertices, IC weighted cascade, k = 50, eps = 0.05
+for _r in (2, 4, 8, 16, 32):
+    WORKLOADS[f"imm-ic-wc-ba1m-r{_r}"] = dict(
+        graph=f"Barabasi-Albert n=10^6 r={_r} (clique r0={_r}, degree-proportional attachment, seed 6)",
+        weights="weighted cascade 1/indeg(v) fp32", model="IC", k=50, eps=0.05, ell=1.0, philox_seed=7)
 WORKLOADS["batch-chunglu-256"] = dict(
     graph="256 Chung-Lu graphs (degree exponent 2.1, 8n draws, dedup), n = round(10^(4+2U)), graph seed 1000+i",
     weights="weighted cascade 1/indeg(v) fp32", model="IC", k="from {10,25,50}", eps="from {0.1,0.2,0.5}", ell=1.0,
@@ -370,16 +379,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+_GRAPH_CACHE = {}
+
+
 def load_workload():
     from paper_2009_07325_gb300 import inputs as I
     name = WORKLOAD["workload"]
+    key = WORKLOAD["graph"] + WORKLOAD["weights"]
+    if key in _GRAPH_CACHE:
+        return _GRAPH_CACHE[key]
     if name == "imm-ic-p001-rmat22":
-        return I.uniform_weights(I.rmat(22, 3), 0.01)
-    if name.endswith("rmat22"):
-        return I.wc_weights(I.rmat(22, 3))
-    if name.endswith("rmat20"):
-        return I.wc_weights(I.rmat(20, 2))
-    return I.wc_weights(I.er(2000, 20000, 1))
+        g = I.uniform_weights(I.rmat(22, 3), 0.01)
+    elif "-ba1m-r" in name:
+        g = I.wc_weights(I.barabasi_albert(10 ** 6, int(name.rsplit("-r", 1)[1]), 6))
+    elif "rmat22" in name:
+        g = I.wc_weights(I.rmat(22, 3))
+    elif name.endswith("rmat20"):
+        g = I.wc_weights(I.rmat(20, 2))
+    else:
+        g = I.wc_weights(I.er(2000, 20000, 1))
+    _GRAPH_CACHE.clear()
+    _GRAPH_CACHE[key] = g
+    return g
 
 
 def model_id():
@@ -503,6 +524,8 @@ def run_ours(args):
 
     mdl = model_id()
     from paper_2009_07325_gb300 import binding
+    if WORKLOAD.get("fresh_final"):
+        ctx.set_option(binding.GIM_OPT_FRESH_FINAL, 1)
     if args.group_budget:   # a fixed schedule (profiler runs: timings under a profiler mislead the tuner)
         ctx.set_option(binding.GIM_OPT_GROUP_BUDGET, args.group_budget)
         budget, tuned_by = args.group_budget, "--group-budget"
@@ -567,7 +590,9 @@ def run_ours(args):
         kern_s = (tk["kernel_ms"] + tk["large_ms"]) / 1e3
         n_launch = max(tk["kernel_launches"] + tk["large_launches"], 1)
         kname = "sample_lt_kernel" if WORKLOAD["model"] == "LT" else "sample_ic_kernel"
-        tr = traffic_record(kname)
+        # the recorded DRAM bytes per RR set hold for the headline graph and weights only
+        same_sets = WORKLOAD["workload"].startswith("imm-ic-wc-rmat22") and "sweep" not in WORKLOAD
+        tr = traffic_record(kname) if same_sets else None
         traffic = None
         if tr is not None:
             per_unit, unit = tr
@@ -630,6 +655,31 @@ def run_case(args):
     return 0
 
 
+SWEEPS = {
+    # runtime against k and against eps on the headline graph (the shapes of Figs. 4-6)
+    "k": [("imm-ic-wc-rmat22", dict(k=k)) for k in (1, 10, 25, 50, 100, 200)],
+    "eps": [("imm-ic-wc-rmat22", dict(eps=e)) for e in (0.5, 0.3, 0.2, 0.1, 0.05)],
+    # density: Barabasi-Albert n = 10^6, r = 2 .. 32 (Fig. 7)
+    "ba": [(f"imm-ic-wc-ba1m-r{r}", {}) for r in (2, 4, 8, 16, 32)],
+}
+
+
+def run_sweep(args):
+    """One benchmark line per point of a sweep (no CPU baseline); single GPU only."""
+    rank, world, _ = dist_env()
+    if world > 1:
+        print("--sweep runs on one GPU", file=sys.stderr)
+        return 2
+    args.no_cpu_baseline = True
+    rc = 0
+    for name, over in SWEEPS[args.sweep]:
+        WORKLOAD.clear()
+        WORKLOAD.update(workload=name, **WORKLOADS[name])
+        WORKLOAD.update(over, sweep=args.sweep)
+        rc = rc or run_ours(args)
+    return rc
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,6 +698,8 @@ def main():
                     help="--case: device bytes for the block-per-set pass scratch (keeps profiler captures small)")
     ap.add_argument("--workload", default="imm-ic-wc-rmat22", choices=sorted(WORKLOADS),
                     help="IMM workload (default: the headline)")
+    ap.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
+                    help="print one line per point of a k, eps or Barabasi-Albert density sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps; the timing rules want at least 3", file=sys.stderr)
@@ -655,6 +707,8 @@ def main():
     WORKLOAD.update(workload=args.workload, **WORKLOADS[args.workload])
     if args.case:
         return run_case(args)
+    if args.sweep and args.impl == "ours":
+        return run_sweep(args)
     if args.workload.startswith("batch-") and args.impl == "ours":
         return run_batch(args)
     if args.workload.startswith("serve-") and args.impl == "ours":

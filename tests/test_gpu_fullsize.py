@@ -1,8 +1,9 @@
 """GPU parity at full size, in the launch configuration the benchmark times.
 
 IMM on R-MAT scale 22 (seed 3, weighted-cascade weights 1/indeg(v) in fp32):
-IC with k = 50, eps = 0.1 and LT with k = 100, eps = 0.05, both with
-l = 1 and Philox seed 7, after the same schedule autotuning the benchmark
+IC with k = 50, eps = 0.1 and LT with k = 100, eps = 0.05; and IC on
+Barabasi-Albert graphs of 10^6 vertices (r = 2 and 32, k = 50, eps = 0.05).
+All with l = 1 and Philox seed 7, after the same schedule autotuning the benchmark
 runs. The oracle cannot redraw a million RR sets in a test's time, so:
 
 * RR sets: a seeded sample of rr_ids plus the largest sets, each redrawn by
@@ -95,4 +96,26 @@ def test_imm_rmat22_ic_p001_full_size():
     assert s[0] == int(np.argmax(cnt)) and gains[0] == cnt.max()
     assert len(set(s.tolist())) == k and all(a >= b for a, b in zip(gains[:-1], gains[1:]))
     assert int(gains.astype(np.int64).sum()) == cov <= R
+    ctx.close()
+
+
+@pytest.mark.parametrize("r", [2, 32])
+def test_imm_barabasi_albert_full_size(r):
+    """The density sweep's end points: Barabasi-Albert n = 10^6 with r = 2 (about 10^7
+    RR sets of a few members) and r = 32 (64 M arcs, sets of tens of members and a few
+    of ten thousand), IC weighted cascade, k = 50, eps = 0.05, as the benchmark runs them."""
+    g = I.wc_weights(I.barabasi_albert(10 ** 6, r, 6))
+    k, eps = 50, 0.05
+    ctx = Context(0)
+    ctx.load(g)
+    binding.autotune([ctx], [(GIM_IC, k, eps, 1.0, 7)], 20000)
+    res = ctx.imm(GIM_IC, k, eps, 1.0, 7)
+    off, mem = ctx.rr_export()
+    assert len(off) - 1 == res["rr_count"] >= res["theta"]
+    orc = O.Oracle(g)
+    _sampled_sets_match(ctx, orc, GIM_IC, 7, off, mem)
+    orc.load_csr(off, mem)
+    o = orc.imm_replay(k, eps, 1.0)
+    assert res["seeds"].tolist() == o["seeds"].tolist()
+    assert (res["theta"], res["lb"], res["rr_count"]) == (o["theta"], o["lb"], o["rr_count"])
     ctx.close()
