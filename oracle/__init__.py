@@ -93,6 +93,18 @@ def _lib_():
             L.orc_imm_fresh.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_uint64, ctypes.c_int, u32p, u64p, f64p, f64p]
             L.orc_imm_fresh.restype = ctypes.c_int
+            L.orc_mrim.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_uint64, ctypes.c_int, u32p, u64p, f64p, f64p]
+            L.orc_mrim.restype = ctypes.c_int
+            L.orc_mrim_one.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, u32p]
+            L.orc_mrim_one.restype = ctypes.c_int64
+            L.orc_mrim_constants.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                             ctypes.c_double, f64p]
+            L.orc_mrim_constants.restype = None
+            L.orc_set_rounds.argtypes = [vp, ctypes.c_uint32]
+            L.orc_set_rounds.restype = ctypes.c_int
+            L.orc_rounds.argtypes = [vp]
+            L.orc_rounds.restype = ctypes.c_uint32
             L.orc_imm_replay.argtypes = [vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, u32p, u64p, f64p,
                                          f64p]
             L.orc_imm_replay.restype = ctypes.c_int
@@ -127,6 +139,12 @@ def log_binom(n: int, k: int) -> float:
 def imm_constants(n: int, k: int, eps: float, ell: float) -> dict:
     out = np.zeros(5, np.float64)
     _lib_().orc_imm_constants(n, k, eps, ell, out)
+    return dict(ell_prime=out[0], eps_prime=out[1], lambda_prime=out[2], lambda_star=out[3], i_max=int(out[4]))
+
+
+def mrim_constants(n: int, k: int, T: int, eps: float, ell: float) -> dict:
+    out = np.zeros(5, np.float64)
+    _lib_().orc_mrim_constants(n, k, T, eps, ell, out)
     return dict(ell_prime=out[0], eps_prime=out[1], lambda_prime=out[2], lambda_star=out[3], i_max=int(out[4]))
 
 
@@ -209,10 +227,30 @@ class Oracle:
         rounds = [dict(x=r[0], theta_i=int(r[1]), covered=int(r[2]), rr_count=int(r[3])) for r in tr]
         return dict(seeds=seeds, theta=int(theta[0]), lb=float(lb[0]), rounds=rounds, rr_count=self.rr_count)
 
+    def mrim(self, model: int, T: int, k: int, eps: float, ell: float, seed: int, threads: int = 1):
+        """Multi-round IM (CR-NAIMM): k*T seeds t*n + v in pick order."""
+        seeds = np.zeros(k * T, np.uint32)
+        theta = np.zeros(1, np.uint64)
+        lb = np.zeros(1, np.float64)
+        trace = np.zeros(4 * 64, np.float64)
+        rc = self.L.orc_mrim(self.h, model, T, k, eps, ell, seed, threads, seeds, theta, lb, trace)
+        if rc < 0:
+            raise RuntimeError(f"oracle mrim failed ({rc})")
+        tr = trace[: 4 * min(rc, 64)].reshape(-1, 4)
+        rounds = [dict(x=r[0], theta_i=int(r[1]), covered=int(r[2]), rr_count=int(r[3])) for r in tr]
+        return dict(seeds=seeds, theta=int(theta[0]), lb=float(lb[0]), rounds=rounds, rr_count=self.rr_count)
+
+    def mrim_one(self, model: int, T: int, seed: int, j: int) -> np.ndarray:
+        out = np.zeros(self.n * T, np.uint32)
+        s = self.L.orc_mrim_one(self.h, model, T, seed, j, out)
+        if s < 0:
+            raise ValueError(f"mrim_one failed ({s})")
+        return out[:s].copy()
+
     def imm_replay(self, k: int, eps: float, ell: float):
         """IMM (Alg. 2 then Alg. 1) with every sampling step served by a prefix of
         the loaded collection; |R| is left at the prefix IMM used."""
-        seeds = np.zeros(k, np.uint32)
+        seeds = np.zeros(k * self.rounds, np.uint32)
         theta = np.zeros(1, np.uint64)
         lb = np.zeros(1, np.float64)
         trace = np.zeros(4 * 64, np.float64)
@@ -241,14 +279,25 @@ class Oracle:
         self.L.orc_export(self.h, off, mem)
         return off, mem[: self.store_size]
 
+    @property
+    def rounds(self) -> int:
+        return int(self.L.orc_rounds(self.h))
+
+    def set_rounds(self, T: int) -> None:
+        """T rounds for an empty collection (multi-round sets, or before loading one)."""
+        if self.L.orc_set_rounds(self.h, T) != 0:
+            raise ValueError("set_rounds needs an empty collection and n*T < 2^32 - 1")
+
     def counts(self) -> np.ndarray:
-        out = np.zeros(self.n, np.uint32)
+        out = np.zeros(self.n * self.rounds, np.uint32)
         self.L.orc_counts(self.h, out)
         return out
 
     def greedy(self, k: int):
-        seeds = np.zeros(k, np.uint32)
-        gains = np.zeros(k, np.uint32)
+        """k seeds (k per round, k*T picks, when the collection has T > 1 rounds)."""
+        kt = k * self.rounds
+        seeds = np.zeros(kt, np.uint32)
+        gains = np.zeros(kt, np.uint32)
         cov = self.L.orc_greedy(self.h, k, seeds, gains)
         if cov < 0:
             raise ValueError("greedy failed")

@@ -27,6 +27,11 @@
  *    paper defers to that work (Sec. II-E, Alg. 2). Sampling stops once
  *    |R| >= ceil(theta) (Alg. 2 and Alg. 6 print the loop condition
  *    inverted). RR sets drawn during the lower-bound search are reused.
+ *  - Multi-round IM (Sec. IV-H): round t of multi-round RR set j uses
+ *    rr_id t * 2^32 + j with the root of RR set j; elements t * n + v; the
+ *    greedy picks k per round; the constants use T ln C(n, k) and the
+ *    partition-matroid guarantee 1/2 (Sun et al.'s own rules are not in
+ *    the paper: parity unpinned for those constants).
  *
  * parity unpinned: the exact IMM constants (lambda', lambda*) against
  * Tang et al.'s own code, which the paper does not print. Everything else
@@ -109,6 +114,7 @@ typedef struct orc {
   uint64_t seed;
   uint64_t count;      /* |R| */
   uint64_t ctr_base;   /* RR set at position j is drawn with rr_id ctr_base + j (0 except in a fresh final phase) */
+  uint32_t rounds;     /* T: 1 for IM; T > 1 for multi-round IM, whose elements are t*n + v */
   uint64_t cap_sets, cap_members;
   uint64_t *rr_off;    /* count+1 */
   uint32_t *members;   /* rr_off[count] */
@@ -157,6 +163,7 @@ orc *orc_create(uint32_t n, uint64_t m, const uint64_t *off, const uint32_t *src
   if (m) { memcpy(g->src, src, m * sizeof(uint32_t)); memcpy(g->w, w, m * sizeof(float)); }
   lt_thresholds(g, g->cum, &g->lt_ok);
   g->model = -1;
+  g->rounds = 1;
   return g;
 }
 
@@ -180,8 +187,8 @@ static int cmp_u32(const void *a, const void *b) {
  * (n bytes, all zero on entry and on return) and `out` (n entries) are
  * caller scratch. Returns |RR_j|; out holds the members in ascending order.
  */
-static uint32_t rr_ic(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited, uint32_t *out) {
-  uint32_t root = orc_root(seed, j, g->n);
+static uint32_t rr_ic_from(const orc *g, uint64_t seed, uint32_t root, uint64_t j, uint8_t *visited,
+                           uint32_t *out) {
   uint32_t head = 0, tail = 0;
   out[tail++] = root;
   visited[root] = 1;
@@ -201,14 +208,19 @@ static uint32_t rr_ic(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited,
   return tail;
 }
 
+static uint32_t rr_ic(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited, uint32_t *out) {
+  return rr_ic_from(g, seed, orc_root(seed, j, g->n), j, visited, out);
+}
+
 /*
  * LT RR set j (Sec. III-G): at each vertex one uniform draw selects at most
  * one live in-edge (the edge whose threshold interval contains the draw);
  * the walk moves to its source and stops when no edge is selected or the
  * source was already visited. Same scratch contract as rr_ic.
  */
-static uint32_t rr_lt(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited, uint32_t *out) {
-  uint32_t x = orc_root(seed, j, g->n);
+static uint32_t rr_lt_from(const orc *g, uint64_t seed, uint32_t root, uint64_t j, uint8_t *visited,
+                           uint32_t *out) {
+  uint32_t x = root;
   uint32_t size = 0;
   out[size++] = x;
   visited[x] = 1;
@@ -227,6 +239,41 @@ static uint32_t rr_lt(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited,
   for (uint32_t i = 0; i < size; ++i) visited[out[i]] = 0;
   qsort(out, size, sizeof(uint32_t), cmp_u32);
   return size;
+}
+
+static uint32_t rr_lt(const orc *g, uint64_t seed, uint64_t j, uint8_t *visited, uint32_t *out) {
+  return rr_lt_from(g, seed, orc_root(seed, j, g->n), j, visited, out);
+}
+
+/*
+ * Multi-round RR set j (Sec. IV-H, CR-NAIMM of Sun et al.): one root, drawn as
+ * for RR set j, and T independent reverse traversals from it, round t in the
+ * live-edge world of rr_id t * 2^32 + j (round 0 is RR set j itself). The
+ * elements are (vertex, round) pairs, numbered t * n + v; out (T * n entries)
+ * receives them in ascending order (round-major, then vertex).
+ */
+static uint32_t rr_multi(const orc *g, int model, uint64_t seed, uint64_t j, uint32_t T, uint8_t *visited,
+                         uint32_t *out) {
+  const uint32_t root = orc_root(seed, j, g->n);
+  uint32_t size = 0;
+  for (uint32_t t = 0; t < T; ++t) {
+    const uint64_t id = ((uint64_t)t << 32) | j;
+    const uint32_t s = model == 0 ? rr_ic_from(g, seed, root, id, visited, out + size)
+                                  : rr_lt_from(g, seed, root, id, visited, out + size);
+    for (uint32_t i = 0; i < s; ++i) out[size + i] += t * g->n;
+    size += s;
+  }
+  return size;
+}
+
+/* One multi-round RR set on its own (T * n entries of out). */
+int64_t orc_mrim_one(const orc *g, int model, uint32_t T, uint64_t seed, uint64_t j, uint32_t *out) {
+  if ((model == 1 && !g->lt_ok) || T < 1 || j >= (1ull << 32)) return -1;
+  uint8_t *visited = (uint8_t *)calloc(g->n, 1);
+  if (!visited) return -2;
+  uint32_t s = rr_multi(g, model, seed, j, T, visited, out);
+  free(visited);
+  return s;
 }
 
 /* One RR set, computed on its own (used for sampled parity at full size). */
@@ -272,6 +319,7 @@ typedef struct { uint64_t n_sets, n_members, cap; uint32_t *mem; uint32_t *sizes
  */
 int orc_sample(orc *g, int model, uint64_t seed, uint64_t count, int threads) {
   if (g->count > 0 && (g->model != model || g->seed != seed)) return -1;
+  if (g->rounds > 1 && (g->ctr_base != 0 || g->count + count > (1ull << 32))) return -1;
   if (model == 1 && !g->lt_ok) return -1;
   if (count == 0) return 0;
   g->model = model;
@@ -287,7 +335,7 @@ int orc_sample(orc *g, int model, uint64_t seed, uint64_t count, int threads) {
     uint64_t a = j0 + count * (uint64_t)t / (uint64_t)threads;
     uint64_t b = j0 + count * (uint64_t)(t + 1) / (uint64_t)threads;
     uint8_t *visited = (uint8_t *)calloc(g->n, 1);
-    uint32_t *out = (uint32_t *)malloc((size_t)g->n * sizeof(uint32_t));
+    uint32_t *out = (uint32_t *)malloc((size_t)g->n * g->rounds * sizeof(uint32_t));
     chunk_buf *c = &cb[t];
     c->cap = 1 << 16;
     c->mem = (uint32_t *)malloc(c->cap * sizeof(uint32_t));
@@ -295,7 +343,9 @@ int orc_sample(orc *g, int model, uint64_t seed, uint64_t count, int threads) {
     if (!visited || !out || !c->mem || !c->sizes) { fail = 1; }
     for (uint64_t j = a; j < b && !fail; ++j) {
       const uint64_t id = g->ctr_base + j;
-      uint32_t s = model == 0 ? rr_ic(g, seed, id, visited, out) : rr_lt(g, seed, id, visited, out);
+      uint32_t s = g->rounds > 1 ? rr_multi(g, model, seed, j, g->rounds, visited, out)
+                   : model == 0  ? rr_ic(g, seed, id, visited, out)
+                                 : rr_lt(g, seed, id, visited, out);
       if (c->n_members + s > c->cap) {
         uint64_t nc = c->cap;
         while (nc < c->n_members + s) nc *= 2;
@@ -335,8 +385,9 @@ int orc_sample(orc *g, int model, uint64_t seed, uint64_t count, int threads) {
  * Returns 0, -1 (a member >= n) or -2 (out of memory).
  */
 int orc_load_collection(orc *g, uint64_t count, const uint64_t *offsets, const uint32_t *members) {
+  const uint64_t universe = (uint64_t)g->n * g->rounds;
   for (uint64_t z = 0; z < offsets[count]; ++z)
-    if (members[z] >= g->n) return -1;
+    if (members[z] >= universe) return -1;
   if (grow_sets(g, count) || grow_members(g, offsets[count])) return -2;
   memcpy(g->rr_off, offsets, (count + 1) * sizeof(uint64_t));
   memcpy(g->members, members, offsets[count] * sizeof(uint32_t));
@@ -347,7 +398,15 @@ int orc_load_collection(orc *g, uint64_t count, const uint64_t *offsets, const u
   return 0;
 }
 
-void orc_reset(orc *g) { g->count = 0; g->rr_off[0] = 0; g->model = -1; g->ctr_base = 0; }
+void orc_reset(orc *g) { g->count = 0; g->rr_off[0] = 0; g->model = -1; g->ctr_base = 0; g->rounds = 1; }
+
+/* Sets T for an empty collection (multi-round sets, or a multi-round collection to load). */
+int orc_set_rounds(orc *g, uint32_t T) {
+  if (g->count != 0 || T < 1 || (uint64_t)g->n * T >= 0xFFFFFFFFull) return -1;
+  g->rounds = T;
+  return 0;
+}
+uint32_t orc_rounds(const orc *g) { return g->rounds; }
 uint64_t orc_rr_count(const orc *g) { return g->count; }
 uint64_t orc_store_size(const orc *g) { return g->rr_off[g->count]; }
 
@@ -358,7 +417,7 @@ void orc_export(const orc *g, uint64_t *offsets, uint32_t *members) {
 
 /* Occur of Sec. III-B: the number of RR sets each vertex belongs to. */
 void orc_counts(const orc *g, uint32_t *cnt) {
-  memset(cnt, 0, (size_t)g->n * sizeof(uint32_t));
+  memset(cnt, 0, (size_t)g->n * g->rounds * sizeof(uint32_t));
   for (uint64_t z = 0; z < g->rr_off[g->count]; ++z) cnt[g->members[z]]++;
 }
 
@@ -370,37 +429,46 @@ void orc_counts(const orc *g, uint32_t *cnt) {
  * contain a vertex are found through a per-vertex list of set ids built
  * once up front. Returns the number of covered RR sets, or -1 on allocation
  * failure / k out of range.
+ *
+ * With T = rounds > 1 (multi-round IM, Sec. IV-H) the elements are the T*n
+ * (vertex, round) pairs and the seed sets are constrained to k per round (a
+ * partition matroid): k*T picks, each the best element among the rounds that
+ * still have fewer than k seeds, the same tie rule. seeds/gains hold k*T
+ * entries in pick order.
  */
 int64_t orc_greedy(const orc *g, uint32_t k, uint32_t *seeds, uint32_t *gains) {
-  const uint32_t n = g->n;
+  const uint32_t n = g->n, T = g->rounds;
+  const uint64_t U = (uint64_t)n * T;
   const uint64_t R = g->count, Z = g->rr_off[R];
   if (k < 1 || k > n) return -1;
-  uint32_t *cnt = (uint32_t *)calloc(n, sizeof(uint32_t));
-  uint64_t *lst_off = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
-  uint64_t *fill = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+  uint32_t *cnt = (uint32_t *)calloc(U, sizeof(uint32_t));
+  uint64_t *lst_off = (uint64_t *)calloc((size_t)U + 1, sizeof(uint64_t));
+  uint64_t *fill = (uint64_t *)malloc(((size_t)U + 1) * sizeof(uint64_t));
   uint64_t *lst = (uint64_t *)malloc((Z ? Z : 1) * sizeof(uint64_t));
   uint8_t *covered = (uint8_t *)calloc(R ? R : 1, 1);
-  uint8_t *selected = (uint8_t *)calloc(n, 1);
-  if (!cnt || !lst_off || !fill || !lst || !covered || !selected) {
-    free(cnt); free(lst_off); free(fill); free(lst); free(covered); free(selected);
+  uint8_t *selected = (uint8_t *)calloc(U, 1);
+  uint32_t *per_round = (uint32_t *)calloc(T, sizeof(uint32_t));
+  if (!cnt || !lst_off || !fill || !lst || !covered || !selected || !per_round) {
+    free(cnt); free(lst_off); free(fill); free(lst); free(covered); free(selected); free(per_round);
     return -1;
   }
   for (uint64_t z = 0; z < Z; ++z) cnt[g->members[z]]++;
-  for (uint32_t x = 0; x < n; ++x) lst_off[x + 1] = lst_off[x] + cnt[x];
-  memcpy(fill, lst_off, ((size_t)n + 1) * sizeof(uint64_t));
+  for (uint64_t x = 0; x < U; ++x) lst_off[x + 1] = lst_off[x] + cnt[x];
+  memcpy(fill, lst_off, ((size_t)U + 1) * sizeof(uint64_t));
   for (uint64_t j = 0; j < R; ++j)
     for (uint64_t z = g->rr_off[j]; z < g->rr_off[j + 1]; ++z) lst[fill[g->members[z]]++] = j;
 
   int64_t n_covered = 0;
-  for (uint32_t t = 0; t < k; ++t) {
-    uint32_t best = UINT32_MAX;
-    for (uint32_t x = 0; x < n; ++x) {
-      if (selected[x]) continue;
-      if (best == UINT32_MAX || cnt[x] > cnt[best]) best = x;
+  for (uint32_t t = 0; t < k * T; ++t) {
+    uint64_t best = UINT64_MAX;
+    for (uint64_t x = 0; x < U; ++x) {
+      if (selected[x] || per_round[x / n] == k) continue;
+      if (best == UINT64_MAX || cnt[x] > cnt[best]) best = x;
     }
-    seeds[t] = best;
+    seeds[t] = (uint32_t)best;
     if (gains) gains[t] = cnt[best];
     selected[best] = 1;
+    per_round[best / n]++;
     for (uint64_t i = lst_off[best]; i < lst_off[best + 1]; ++i) {
       uint64_t j = lst[i];
       if (covered[j]) continue;
@@ -409,7 +477,7 @@ int64_t orc_greedy(const orc *g, uint32_t k, uint32_t *seeds, uint32_t *gains) {
       for (uint64_t z = g->rr_off[j]; z < g->rr_off[j + 1]; ++z) cnt[g->members[z]]--;
     }
   }
-  free(cnt); free(lst_off); free(fill); free(lst); free(covered); free(selected);
+  free(cnt); free(lst_off); free(fill); free(lst); free(covered); free(selected); free(per_round);
   return n_covered;
 }
 
@@ -429,21 +497,33 @@ double orc_log_binom(uint32_t n, uint32_t k) {
  * lambda*, i_max}. ell' = ell (1 + ln2 / ln n) gives success probability
  * 1 - 1/n^ell; eps' = sqrt(2) eps is the (1 + sqrt(2) eps) of Alg. 2.
  */
-void orc_imm_constants(uint32_t n, uint32_t k, double eps, double ell, double out[5]) {
+/*
+ * The same constants for multi-round IM with T rounds of k seeds (CR-NAIMM,
+ * Sec. IV-H). The paper leaves them to Sun et al.; reading: the number of
+ * feasible seed sets is C(n, k)^T, so ln C(n, k) becomes T ln C(n, k), and the
+ * greedy's guarantee over the partition matroid is 1/2, which takes the place
+ * of 1 - 1/e in lambda* (alpha, beta). With T = 1 they are IMM's constants
+ * exactly. The estimate stays n F_R(S): one root per set, drawn over V.
+ */
+void orc_mrim_constants(uint32_t n, uint32_t k, uint32_t T, double eps, double ell, double out[5]) {
   const double ln_n = log((double)n);
   const double ellp = ell * (1.0 + log(2.0) / ln_n);
   const double epsp = sqrt(2.0) * eps;
-  const double lnC = orc_log_binom(n, k);
+  const double lnC = (double)T * orc_log_binom(n, k);
   const double lam_prime = (2.0 + 2.0 * epsp / 3.0) * (lnC + ellp * ln_n + log(log2((double)n))) * (double)n /
                            (epsp * epsp);
-  const double one_m_inv_e = 1.0 - exp(-1.0);
+  const double gamma = T == 1 ? 1.0 - exp(-1.0) : 0.5;
   const double alpha = sqrt(ellp * ln_n + log(2.0));
-  const double beta = sqrt(one_m_inv_e * (lnC + ellp * ln_n + log(2.0)));
-  const double t = one_m_inv_e * alpha + beta;
+  const double beta = sqrt(gamma * (lnC + ellp * ln_n + log(2.0)));
+  const double t = gamma * alpha + beta;
   const double lam_star = 2.0 * (double)n * t * t / (eps * eps);
   int lg = 0;
   while (((uint64_t)n >> (lg + 1)) != 0) lg++; /* floor(log2 n), shift kept below 64 bits */
   out[0] = ellp; out[1] = epsp; out[2] = lam_prime; out[3] = lam_star; out[4] = (double)(lg - 1);
+}
+
+void orc_imm_constants(uint32_t n, uint32_t k, double eps, double ell, double out[5]) {
+  orc_mrim_constants(n, k, 1, eps, ell, out);
 }
 
 /*
@@ -471,7 +551,7 @@ static int imm_core(orc *g, int model, uint32_t k, double eps, double ell, uint6
                     uint64_t avail, int fresh, uint32_t *seeds, uint64_t *theta_out, double *lb_out,
                     double *trace) {
   double c[5];
-  orc_imm_constants(g->n, k, eps, ell, c);
+  orc_mrim_constants(g->n, k, g->rounds, eps, ell, c);
   const double epsp = c[1], lam_prime = c[2], lam_star = c[3];
   const int i_max = (int)c[4];
   double LB = 1.0;
@@ -519,6 +599,7 @@ int orc_imm(orc *g, int model, uint32_t k, double eps, double ell, uint64_t seed
             uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
   if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
   if (g->count != 0) return -1;
+  g->rounds = 1;
   return imm_core(g, model, k, eps, ell, seed, threads, 0, 0, seeds, theta_out, lb_out, trace);
 }
 
@@ -534,6 +615,7 @@ int orc_imm_fresh(orc *g, int model, uint32_t k, double eps, double ell, uint64_
                   uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
   if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
   if (g->count != 0) return -1;
+  g->rounds = 1;
   return imm_core(g, model, k, eps, ell, seed, threads, 0, 1, seeds, theta_out, lb_out, trace);
 }
 
@@ -554,6 +636,20 @@ int orc_imm_replay(orc *g, uint32_t k, double eps, double ell, uint32_t *seeds, 
   const int rc = imm_core(g, 0, k, eps, ell, 0, 1, avail, 0, seeds, theta_out, lb_out, trace);
   if (rc < 0) g->count = avail;
   return rc;
+}
+
+/*
+ * Multi-round IM (Sec. IV-H, CR-NAIMM): IMM's steps over multi-round RR sets
+ * (rr_multi) with the constants of orc_mrim_constants and the greedy under k
+ * seeds per round. seeds: k*T element ids t*n + v in pick order. The store
+ * must start empty; afterwards it holds the multi-round collection (T stays
+ * set until orc_reset). Returns the lower-bound rounds or a negative error.
+ */
+int orc_mrim(orc *g, int model, uint32_t T, uint32_t k, double eps, double ell, uint64_t seed, int threads,
+             uint32_t *seeds, uint64_t *theta_out, double *lb_out, double *trace) {
+  if (k < 1 || k > g->n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0) || g->n < 2) return -3;
+  if (g->count != 0 || orc_set_rounds(g, T) != 0) return -1;
+  return imm_core(g, model, k, eps, ell, seed, threads, 0, 0, seeds, theta_out, lb_out, trace);
 }
 
 int orc_max_threads(void) {
