@@ -58,6 +58,9 @@ WORKLOADS = {
     "imm-ic-wc-rmat22-fresh": dict(graph=_RMAT.format(s=22, seed=3), weights="weighted cascade 1/indeg(v) fp32",
                                    model="IC", k=50, eps=0.1, ell=1.0, philox_seed=7, fresh_final=True),
 }
+# multi-round IM (Sec. IV-H, CR-NAIMM) with the paper's T = 5 rounds, k = 10 per round, eps = 0.1
+WORKLOADS["mrim-ic-wc-rmat22-T5"] = dict(graph=_RMAT.format(s=22, seed=3), weights="weighted cascade 1/indeg(v) fp32",
+                                         model="IC", k=10, eps=0.1, ell=1.0, philox_seed=7, rounds=5)
 # Barabasi-Albert density sweep (Sec. IV-F): n = 10^6, r = 2 .. 32 undirected edges per new vertex
 # (both directions stored), clique of r0 = r vertices, IC weighted cascade, k = 50, eps = 0.05
 for _r in (2, 4, 8, 16, 32):
@@ -467,15 +470,19 @@ def cpu_baseline(graph, budget_s: float = 12.0):
     O.build()
     th = max(1, O.max_threads())
     o = O.Oracle(graph)
+    T = WORKLOAD.get("rounds", 0)
+    if T:
+        o.set_rounds(T)
     t0 = time.perf_counter()
-    chunk = 4000
+    chunk = 4000 if not T else 500
     while time.perf_counter() - t0 < budget_s:
         o.sample(O.LT if WORKLOAD["model"] == "LT" else O.IC, WORKLOAD["philox_seed"], chunk, th)
     o.greedy(WORKLOAD["k"])
     dt = time.perf_counter() - t0
     n = o.rr_count
+    kind = f"{T}-round {WORKLOAD['model']}" if T else WORKLOAD["model"]
     return {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle",
-            "sample": f"{n} {WORKLOAD['model']} RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
+            "sample": f"{n} {kind} RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
                       f"{dt:.1f} s"}
 
 
@@ -532,8 +539,17 @@ def run_ours(args):
     else:
         budget, _ = binding.autotune([ctx], [(mdl, k, eps, ell, seed)], 20000)   # schedule for this profile
         tuned_by = "gim_autotune"
+    T = WORKLOAD.get("rounds", 0)
+
+    def run_once():
+        return ctx.mrim(mdl, T, k, eps, ell, seed) if T else ctx.imm(mdl, k, eps, ell, seed)
+
+    def vertex_counts():   # occurrences per vertex (a multi-round collection counts per (vertex, round))
+        c = ctx.coverage()
+        return c.reshape(T, -1).sum(axis=0) if T else c
+
     for _ in range(args.warmup):
-        ctx.imm(mdl, k, eps, ell, seed)
+        run_once()
 
     ctx.reset_timings()
     launches0 = ctx.launch_count()
@@ -548,7 +564,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = ctx.imm(mdl, k, eps, ell, seed)
+            r = run_once()
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -558,7 +574,7 @@ def run_ours(args):
             rr_sets += r["rr_count"]
             thetas.append(r["theta"])
             members_total += ctx.rr_count()[1]
-            cov = ctx.coverage()
+            cov = vertex_counts()
             alg_bytes += algorithmic_bytes(cov, indeg)
             coins += coin_count(cov, indeg)
     torch.cuda.synchronize()
@@ -579,11 +595,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.graph_load(g.n, off_p, src_p, w_p)
-        r = ctx.imm(mdl, k, eps, ell, seed)
+        r = run_once()
         e2e_t += time.perf_counter() - t0
         e2e_units += r["rr_count"]
     e2e_u, e2e_s = aggregate(float(e2e_units), e2e_t)
-    d2h = 4 * k + 8 + 8
+    d2h = 4 * k * max(T, 1) + 8 + 8
 
     if rank == 0:
         hbm_peak, peak_kind = measured_peaks()

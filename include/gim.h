@@ -103,8 +103,26 @@ gim_status gim_graph_lt_valid(gim_ctx *ctx, int *out);
  */
 gim_status gim_sample_rr(gim_ctx *ctx, gim_model model, uint64_t count, uint64_t seed);
 
-/* Empties the RR collection (keeps the graph). */
+/* Empties the RR collection (keeps the graph); it becomes a plain (1-round) collection. */
 gim_status gim_reset_rr(gim_ctx *ctx);
+
+/*
+ * Makes the empty collection a multi-round collection of T rounds
+ * (multi-round IM, Sec. IV-H; CR-NAIMM of Sun et al.). Multi-round RR set j
+ * has the root of RR set j and T independent reverse traversals from it
+ * (BFS under IC, walk under LT): round t runs in the live-edge world of
+ * rr_id t * 2^32 + j (Philox counter words j_lo = j, j_hi = t; round 0 is RR
+ * set j itself), and its vertices v are stored as elements t * n + v. Then
+ * gim_sample_rr appends such sets, gim_select_seeds takes k seeds per round,
+ * gim_coverage_export copies T * n element counts and the exports return
+ * element ids. T = 1 is a plain collection.
+ * Errors: GIM_ERR_STATE (no graph, or the collection is not empty),
+ * GIM_ERR_ARG (T = 0, T > 32, or n * T >= 2^32 - 1), GIM_ERR_OOM, GIM_ERR_CUDA.
+ */
+gim_status gim_rr_set_rounds(gim_ctx *ctx, uint32_t rounds);
+
+/* T of the collection (1 for plain RR sets). Errors: GIM_ERR_ARG (null argument). */
+gim_status gim_rr_rounds(gim_ctx *ctx, uint32_t *rounds_out);
 
 /*
  * Greedy maximum coverage over the collection (the maximum-coverage step of Alg. 1;
@@ -117,6 +135,10 @@ gim_status gim_reset_rr(gim_ctx *ctx);
  *   gains_out:   nullable, k entries; the marginal coverage of each seed.
  * The collection is not modified. Errors: GIM_ERR_ARG (k = 0, k > n, or
  * seeds_out NULL), GIM_ERR_STATE (no graph), GIM_ERR_OOM, GIM_ERR_CUDA.
+ * On a multi-round collection of T rounds the candidates are the T * n
+ * elements, a round takes at most k seeds, and there are k * T picks (each
+ * the best element among the rounds not yet full); seeds_out and gains_out
+ * then hold k * T entries (element ids t * n + v).
  */
 gim_status gim_select_seeds(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *covered_out,
                             uint32_t *gains_out);
@@ -137,6 +159,24 @@ gim_status gim_select_seeds(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint6
  */
 gim_status gim_imm(gim_ctx *ctx, gim_model model, uint32_t k, double eps, double ell, uint64_t seed,
                    uint32_t *seeds_out, uint64_t *theta_out, double *lb_out);
+
+/*
+ * Multi-round IM (Sec. IV-H; the CR-NAIMM algorithm of Sun et al., KDD
+ * 2018): gim_imm's steps over multi-round RR sets of `rounds` = T rounds
+ * (see gim_rr_set_rounds), every selection taking k seeds per round. The
+ * paper defers the constants to Sun et al.; this library's reading: the
+ * number of feasible seed sets is C(n, k)^T, so ln C(n, k) becomes
+ * T ln C(n, k), and the greedy's guarantee over that partition matroid, 1/2,
+ * replaces 1 - 1/e in lambda*. LB and theta are as in gim_imm; the estimate
+ * is n F_R(S), F_R the covered fraction of the multi-round sets. T = 1 is
+ * gim_imm exactly. GIM_OPT_FRESH_FINAL does not apply (sets are reused).
+ * Empties the collection first and leaves the final multi-round collection.
+ *   seeds_out: k * T entries (required), element ids t * n + v in pick order.
+ *   theta_out, lb_out: nullable.
+ * Errors: as gim_imm, plus GIM_ERR_ARG (T = 0, T > 32, n * T >= 2^32 - 1).
+ */
+gim_status gim_mrim(gim_ctx *ctx, gim_model model, uint32_t rounds, uint32_t k, double eps, double ell,
+                    uint64_t seed, uint32_t *seeds_out, uint64_t *theta_out, double *lb_out);
 
 /*
  * Greedy maximum coverage that allocates no memory. The paper has no
@@ -331,7 +371,8 @@ gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_
  */
 gim_status gim_rr_get(gim_ctx *ctx, uint64_t rr_id, uint32_t *members_out, uint32_t cap, uint32_t *len_out);
 
-/* Copies the n occurrence counts (RR sets containing each vertex). */
+/* Copies the occurrence counts (RR sets containing each vertex): n entries,
+   or T * n (one per element) for a multi-round collection of T rounds. */
 gim_status gim_coverage_export(gim_ctx *ctx, uint32_t *cnt_out);
 
 /*

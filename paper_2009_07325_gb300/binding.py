@@ -50,6 +50,10 @@ SIGNATURES = {
     "gim_graph_lt_valid": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "gim_sample_rr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]),
     "gim_reset_rr": (ctypes.c_int, [_vp]),
+    "gim_rr_set_rounds": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "gim_rr_rounds": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
+    "gim_mrim": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_uint64, _c_u32p, _c_u64p, _c_f64p]),
     "gim_select_seeds": (ctypes.c_int, [_vp, ctypes.c_uint32, _c_u32p, _c_u64p, _c_u32p]),
     "gim_imm": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                ctypes.c_uint64, _c_u32p, _c_u64p, _c_f64p]),
@@ -173,9 +177,20 @@ class Context:
     def reset_rr(self):
         self._check(self.L.gim_reset_rr(self.h), "gim_reset_rr")
 
+    def set_rounds(self, T: int):
+        """Makes the empty collection a multi-round collection of T rounds."""
+        self._check(self.L.gim_rr_set_rounds(self.h, T), "gim_rr_set_rounds")
+
+    def rounds(self) -> int:
+        t = ctypes.c_uint32(0)
+        self._check(self.L.gim_rr_rounds(self.h, ctypes.byref(t)), "gim_rr_rounds")
+        return int(t.value)
+
     def select_seeds(self, k: int):
-        seeds = np.zeros(k, np.uint32)
-        gains = np.zeros(k, np.uint32)
+        """k seeds (k per round, k*T entries, on a multi-round collection)."""
+        kt = k * self.rounds()
+        seeds = np.zeros(kt, np.uint32)
+        gains = np.zeros(kt, np.uint32)
         cov = ctypes.c_uint64(0)
         self._check(self.L.gim_select_seeds(self.h, k, _p(seeds, _c_u32p), ctypes.byref(cov), _p(gains, _c_u32p)),
                     "gim_select_seeds")
@@ -187,6 +202,15 @@ class Context:
         lb = ctypes.c_double(0)
         self._check(self.L.gim_imm(self.h, model, k, eps, ell, seed, _p(seeds, _c_u32p), ctypes.byref(theta),
                                    ctypes.byref(lb)), "gim_imm")
+        return dict(seeds=seeds, theta=int(theta.value), lb=float(lb.value), rr_count=self.rr_count()[0])
+
+    def mrim(self, model: int, T: int, k: int, eps: float, ell: float, seed: int):
+        """Multi-round IM (CR-NAIMM): k*T seeds as element ids t*n + v, in pick order."""
+        seeds = np.zeros(k * T, np.uint32)
+        theta = ctypes.c_uint64(0)
+        lb = ctypes.c_double(0)
+        self._check(self.L.gim_mrim(self.h, model, T, k, eps, ell, seed, _p(seeds, _c_u32p), ctypes.byref(theta),
+                                    ctypes.byref(lb)), "gim_mrim")
         return dict(seeds=seeds, theta=int(theta.value), lb=float(lb.value), rr_count=self.rr_count()[0])
 
     def rr_count(self):
@@ -203,9 +227,11 @@ class Context:
         return off, mem[:Z]
 
     def coverage(self) -> np.ndarray:
-        out = np.zeros(max(self.n, 1), np.uint32)
+        """Occurrence counts: n entries, or T*n for a multi-round collection."""
+        u = self.n * self.rounds()
+        out = np.zeros(max(u, 1), np.uint32)
         self._check(self.L.gim_coverage_export(self.h, _p(out, _c_u32p)), "gim_coverage_export")
-        return out[: self.n]
+        return out[:u]
 
     def timings(self) -> dict:
         out = np.zeros(8, np.float64)

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgim.so")
-SOURCES = ["api.cu", "batch.cu", "engine.cu", "graph.cu", "greedy.cu", "sample.cu", "select.cu", "serve.cu", "tune.cu"]
+SOURCES = ["api.cu", "batch.cu", "engine.cu", "graph.cu", "greedy.cu", "mrim.cu", "sample.cu", "select.cu", "serve.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

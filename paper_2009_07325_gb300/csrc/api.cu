@@ -79,17 +79,20 @@ gim_status check_ctx(gim_ctx *ctx) {
   return GIM_OK;
 }
 
+// Greedy selection over the context's collection: k seeds, or k per round
+// (k * T picks over the T * n elements) on a multi-round collection.
 gim_status do_select(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *covered_out, uint32_t *gains_out) {
   if (ctx->R >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "more than 2^32-2 RR sets");
-  // a one-slot batched selection, configured for this graph and the largest k asked so far
-  if (!ctx->msel || ctx->msel_n != ctx->g.n || ctx->msel_k < k) {
+  const uint32_t T = ctx->rounds, U = ctx->g.n * T, picks = k * T;
+  // a one-slot batched selection, configured for this universe and the most picks asked so far
+  if (!ctx->msel || ctx->msel_n != U || ctx->msel_k < picks) {
     delete ctx->msel;
     ctx->msel = new (std::nothrow) MultiSelect();
     if (!ctx->msel) return set_err(ctx, GIM_ERR_OOM, "selection state");
-    const uint32_t kc = std::max(k, ctx->msel_n == ctx->g.n ? ctx->msel_k : 0u);
-    ctx->msel_n = ctx->g.n;
+    const uint32_t kc = std::max(picks, ctx->msel_n == U ? ctx->msel_k : 0u);
+    ctx->msel_n = U;
     ctx->msel_k = 0;
-    gim_status st = ctx->msel->configure(ctx, {ctx->g.n}, {kc});
+    gim_status st = ctx->msel->configure(ctx, {U}, {kc});
     if (st != GIM_OK) return st;
     ctx->msel_k = kc;
   }
@@ -102,14 +105,92 @@ gim_status do_select(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *co
   x.rr_len = ctx->st.rr_len;
   x.cnt = ctx->st.cnt;
   x.buf = &ctx->sel;
-  x.k = k;
+  x.k = picks;
+  if (T > 1) {
+    x.part_n = ctx->g.n;
+    x.part_k = k;
+  }
   std::vector<unsigned long long> cov;
   std::vector<uint32_t> seeds, gains;
   gim_status st = ctx->msel->run(ctx, {x}, ctx->stream, cov, seeds, gains_out ? &gains : nullptr);
   if (st != GIM_OK) return st;
-  std::memcpy(seeds_out, seeds.data(), k * sizeof(uint32_t));
-  if (gains_out) std::memcpy(gains_out, gains.data(), k * sizeof(uint32_t));
+  std::memcpy(seeds_out, seeds.data(), picks * sizeof(uint32_t));
+  if (gains_out) std::memcpy(gains_out, gains.data(), picks * sizeof(uint32_t));
   if (covered_out) *covered_out = cov[0];
+  return GIM_OK;
+}
+
+// IMM (T = 1) or multi-round IM (CR-NAIMM, T > 1): Alg. 2's lower-bound
+// search, then theta sets and the final greedy (Alg. 1). With T > 1 the sets
+// are multi-round RR sets and every selection takes k seeds per round.
+gim_status run_imm(gim_ctx *ctx, gim_model model, uint32_t T, uint32_t k, double eps, double ell, uint64_t seed,
+                   uint32_t *seeds_out, uint64_t *theta_out, double *lb_out) {
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
+  if (model != GIM_IC && model != GIM_LT) return set_err(ctx, GIM_ERR_ARG, "unknown model");
+  if (k == 0 || k > ctx->g.n || !seeds_out) return set_err(ctx, GIM_ERR_ARG, "need 1 <= k <= n and seeds_out");
+  if (!(eps > 0.0 && eps < 1.0)) return set_err(ctx, GIM_ERR_ARG, "eps must be in (0, 1)");
+  if (!(ell > 0.0)) return set_err(ctx, GIM_ERR_ARG, "ell must be > 0");
+  if (model == GIM_LT && !ctx->lt_ok) return set_err(ctx, GIM_ERR_ARG, "graph weights are not valid for LT");
+  if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
+  if (T > 1 && (st = gim_rr_set_rounds(ctx, T)) != GIM_OK) return st;
+
+  const uint32_t n = ctx->g.n;
+  const ImmConst c = mrim_constants(n, k, T, eps, ell);
+  double t_sample = 0, t_select = 0;
+  auto timed = [&](double &acc, auto &&fn) -> gim_status {
+    cudaEventRecord(ctx->ev[4], ctx->stream);
+    gim_status r = fn();
+    cudaEventRecord(ctx->ev[5], ctx->stream);
+    cudaEventSynchronize(ctx->ev[5]);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
+    acc += ms;
+    return r;
+  };
+  auto sample_to = [&](uint64_t target) -> gim_status {
+    if (ctx->R >= target) return GIM_OK;
+    if (target >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "theta above 2^32-2 RR sets");
+    const uint64_t cnt = target - ctx->R;
+    return timed(t_sample, [&] {
+      gim_status r = T > 1 ? mrim_sample(ctx, model, seed, cnt) : sample_range(ctx, model, seed, cnt);
+      if (r == GIM_OK) {
+        ctx->model = model;
+        ctx->seed = seed;
+      }
+      return r;
+    });
+  };
+  double LB = 1.0;
+  int rounds = 0;
+  for (int i = 1; i <= c.i_max; ++i) {
+    const double x = (double)n / std::ldexp(1.0, i);
+    const uint64_t theta_i = (uint64_t)std::ceil(c.lam1 / x);
+    if ((st = sample_to(theta_i)) != GIM_OK) return st;
+    uint64_t cov = 0;
+    if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, &cov, nullptr); })) != GIM_OK) return st;
+    ++rounds;
+    const double est = ((double)n * (double)cov) / (double)ctx->R;
+    if (est >= (1.0 + c.epsp) * x) {
+      LB = est / (1.0 + c.epsp);
+      break;
+    }
+  }
+  const uint64_t theta = (uint64_t)std::ceil(c.lam2 / LB);
+  if (ctx->fresh_final && T == 1) {   // theta new sets, rr_ids 2^63 + j, replace the search's collection
+    if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
+    ctx->jhi = ctx->rhi = 1u << 31;
+  }
+  if ((st = sample_to(theta)) != GIM_OK) return st;
+  if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, nullptr, nullptr); })) != GIM_OK) return st;
+  if (theta_out) *theta_out = theta;
+  if (lb_out) *lb_out = LB;
+  ctx->t_sample_ms = t_sample;
+  ctx->t_select_ms = t_select;
+  ctx->t_wall_ms = ms_since(t0);
+  ctx->lb_rounds = rounds;
   return GIM_OK;
 }
 
@@ -157,6 +238,7 @@ void gim_destroy(gim_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  mrim_release(ctx);
   if (ctx->owns_graph) free_graph(ctx->g);
   dfree(ctx->st.members);
   dfree(ctx->st.rr_start);
@@ -166,6 +248,7 @@ void gim_destroy(gim_ctx *ctx) {
   delete ctx->msel;
   ctx->msel = nullptr;
   if (ctx->shared_held) shared_release(ctx->device);
+  ctx->shared_held = false;
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -248,8 +331,11 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   free_select(ctx->sel);
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
-  ctx->jhi = 0;
+  ctx->jhi = ctx->rhi = 0;
+  ctx->rounds = 1;
+  ctx->cnt_cap = 0;
   CU(cudaMalloc(&ctx->st.cnt, (uint64_t)n * 4 + 16));
+  ctx->cnt_cap = (uint64_t)n + 4;
   CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)n * 4 + 16, s));
   CU(cudaStreamSynchronize(s));
   return GIM_OK;
@@ -276,7 +362,7 @@ gim_status gim_sample_rr(gim_ctx *ctx, gim_model model, uint64_t count, uint64_t
   if (ctx->R + count >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "more than 2^32-2 RR sets");
   if (count == 0) return GIM_OK;
   CU(cudaEventRecord(ctx->ev[0], ctx->stream));
-  st = sample_range(ctx, model, seed, count);
+  st = ctx->rounds > 1 ? mrim_sample(ctx, model, seed, count) : sample_range(ctx, model, seed, count);
   if (st) return st;
   ctx->model = model;
   ctx->seed = seed;
@@ -297,9 +383,37 @@ gim_status gim_reset_rr(gim_ctx *ctx) {
   if (!ctx->has_graph) return GIM_OK;
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
-  ctx->jhi = 0;
-  CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)ctx->g.n * 4, ctx->stream));
+  ctx->jhi = ctx->rhi = 0;
+  CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)ctx->g.n * ctx->rounds * 4, ctx->stream));
+  ctx->rounds = 1;
   CU(cudaStreamSynchronize(ctx->stream));
+  return GIM_OK;
+}
+
+gim_status gim_rr_set_rounds(gim_ctx *ctx, uint32_t T) {
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
+  if (ctx->R != 0) return set_err(ctx, GIM_ERR_STATE, "the collection is not empty; call gim_reset_rr");
+  if (T < 1 || T > kMaxRounds) return set_err(ctx, GIM_ERR_ARG, "rounds must be in [1, %u]", kMaxRounds);
+  const uint64_t U = (uint64_t)ctx->g.n * T;
+  if (U >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "n * rounds must stay below 2^32 - 1");
+  if (ctx->cnt_cap < U + 4) {
+    uint32_t *c = nullptr;
+    CU(cudaMalloc(&c, (U + 4) * 4));
+    cudaFree(ctx->st.cnt);
+    ctx->st.cnt = c;
+    ctx->cnt_cap = U + 4;
+  }
+  CU(cudaMemsetAsync(ctx->st.cnt, 0, (U + 4) * 4, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->rounds = T;
+  return GIM_OK;
+}
+
+gim_status gim_rr_rounds(gim_ctx *ctx, uint32_t *rounds_out) {
+  if (!ctx || !rounds_out) return GIM_ERR_ARG;
+  *rounds_out = ctx->rounds;
   return GIM_OK;
 }
 
@@ -326,72 +440,15 @@ gim_status gim_select_seeds(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint6
 
 gim_status gim_imm(gim_ctx *ctx, gim_model model, uint32_t k, double eps, double ell, uint64_t seed,
                    uint32_t *seeds_out, uint64_t *theta_out, double *lb_out) {
+  return run_imm(ctx, model, 1, k, eps, ell, seed, seeds_out, theta_out, lb_out);
+}
+
+gim_status gim_mrim(gim_ctx *ctx, gim_model model, uint32_t rounds, uint32_t k, double eps, double ell,
+                    uint64_t seed, uint32_t *seeds_out, uint64_t *theta_out, double *lb_out) {
   gim_status st = check_ctx(ctx);
   if (st) return st;
-  const auto t0 = std::chrono::steady_clock::now();
-  if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
-  if (model != GIM_IC && model != GIM_LT) return set_err(ctx, GIM_ERR_ARG, "unknown model");
-  if (k == 0 || k > ctx->g.n || !seeds_out) return set_err(ctx, GIM_ERR_ARG, "need 1 <= k <= n and seeds_out");
-  if (!(eps > 0.0 && eps < 1.0)) return set_err(ctx, GIM_ERR_ARG, "eps must be in (0, 1)");
-  if (!(ell > 0.0)) return set_err(ctx, GIM_ERR_ARG, "ell must be > 0");
-  if (model == GIM_LT && !ctx->lt_ok) return set_err(ctx, GIM_ERR_ARG, "graph weights are not valid for LT");
-  if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
-
-  const uint32_t n = ctx->g.n;
-  const ImmConst c = imm_constants(n, k, eps, ell);
-  double t_sample = 0, t_select = 0;
-  auto timed = [&](double &acc, auto &&fn) -> gim_status {
-    cudaEventRecord(ctx->ev[4], ctx->stream);
-    gim_status r = fn();
-    cudaEventRecord(ctx->ev[5], ctx->stream);
-    cudaEventSynchronize(ctx->ev[5]);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
-    acc += ms;
-    return r;
-  };
-  auto sample_to = [&](uint64_t target) -> gim_status {
-    if (ctx->R >= target) return GIM_OK;
-    if (target >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "theta above 2^32-2 RR sets");
-    const uint64_t cnt = target - ctx->R;
-    return timed(t_sample, [&] {
-      gim_status r = sample_range(ctx, model, seed, cnt);
-      if (r == GIM_OK) {
-        ctx->model = model;
-        ctx->seed = seed;
-      }
-      return r;
-    });
-  };
-  double LB = 1.0;
-  int rounds = 0;
-  for (int i = 1; i <= c.i_max; ++i) {
-    const double x = (double)n / std::ldexp(1.0, i);
-    const uint64_t theta_i = (uint64_t)std::ceil(c.lam1 / x);
-    if ((st = sample_to(theta_i)) != GIM_OK) return st;
-    uint64_t cov = 0;
-    if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, &cov, nullptr); })) != GIM_OK) return st;
-    ++rounds;
-    const double est = ((double)n * (double)cov) / (double)ctx->R;
-    if (est >= (1.0 + c.epsp) * x) {
-      LB = est / (1.0 + c.epsp);
-      break;
-    }
-  }
-  const uint64_t theta = (uint64_t)std::ceil(c.lam2 / LB);
-  if (ctx->fresh_final) {   // theta new sets, rr_ids 2^63 + j, replace the search's collection
-    if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
-    ctx->jhi = 1u << 31;
-  }
-  if ((st = sample_to(theta)) != GIM_OK) return st;
-  if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, nullptr, nullptr); })) != GIM_OK) return st;
-  if (theta_out) *theta_out = theta;
-  if (lb_out) *lb_out = LB;
-  ctx->t_sample_ms = t_sample;
-  ctx->t_select_ms = t_select;
-  ctx->t_wall_ms = ms_since(t0);
-  ctx->lb_rounds = rounds;
-  return GIM_OK;
+  if (rounds < 1 || rounds > kMaxRounds) return set_err(ctx, GIM_ERR_ARG, "rounds must be in [1, %u]", kMaxRounds);
+  return run_imm(ctx, model, rounds, k, eps, ell, seed, seeds_out, theta_out, lb_out);
 }
 
 gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params,
@@ -530,7 +587,8 @@ gim_status gim_coverage_export(gim_ctx *ctx, uint32_t *cnt_out) {
   if (st) return st;
   if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
   if (!cnt_out) return set_err(ctx, GIM_ERR_ARG, "cnt_out is null");
-  CU(cudaMemcpyAsync(cnt_out, ctx->st.cnt, (uint64_t)ctx->g.n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(cnt_out, ctx->st.cnt, (uint64_t)ctx->g.n * ctx->rounds * 4, cudaMemcpyDeviceToHost,
+                     ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return GIM_OK;
 }

@@ -626,6 +626,8 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     g.covered_total = D.covered_total;
     g.stats = D.stats;
     g.bar = D.bar;
+    g.part_n = in[i].part_n;
+    g.part_k = in[i].part_k;
   }
   CU(cudaMemcpyAsync(B.d, B.h.data(), B.ni * sizeof(SelDesc), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(B.gd, B.gh.data(), B.ni * sizeof(GreedyDesc), cudaMemcpyHostToDevice, s));
@@ -647,7 +649,9 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
   for (size_t w = 0; w < B.wave_first.size(); ++w) {
     const uint32_t first = B.wave_first[w];
     const uint32_t count = (w + 1 < B.wave_first.size() ? B.wave_first[w + 1] : B.ni) - first;
-    CU(launch_greedy(B.gd + first, count, B.wave_grid[w], B.sync + B.ni, s));
+    bool part = false;
+    for (uint32_t i = first; i < first + count; ++i) part = part || B.gh[i].part_n != 0;
+    CU(launch_greedy(B.gd + first, count, B.wave_grid[w], B.sync + B.ni, s, part));
     ctx->launches += 1;
   }
   CU(cudaEventRecord(ctx->ev[9], s));
@@ -695,7 +699,8 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
     gim_ctx *c = ctxs[i];
     c->R = c->Z = c->store_used = 0;
     c->model = -1;
-    c->jhi = 0;
+    c->jhi = c->rhi = 0;
+    c->rounds = 1;
     CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
     imm_init(S[i], c->g.n, params[i]);
     ns[i] = c->g.n;
@@ -718,7 +723,7 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
       gim_ctx *c = ctxs[i];
       if (S[i].phase == 1 && c->fresh_final && c->jhi == 0) {   // fresh final phase: rr_ids 2^63 + j
         c->R = c->Z = c->store_used = 0;
-        c->jhi = 1u << 31;
+        c->jhi = c->rhi = 1u << 31;
         CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
       }
       const uint64_t target = imm_target(S[i], c->g.n);

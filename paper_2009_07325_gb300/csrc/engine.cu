@@ -77,17 +77,21 @@ template cudaError_t grow_copy<uint64_t>(uint64_t *&, uint64_t &, uint64_t, uint
 template cudaError_t grow_copy<unsigned long long>(unsigned long long *&, uint64_t &, uint64_t, uint64_t,
                                                    cudaStream_t);
 
-// IMM constants (Tang, Shi, Xiao 2015) in a fixed evaluation order.
-ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell) {
+// IMM constants (Tang, Shi, Xiao 2015) in a fixed evaluation order. With T
+// rounds of k seeds (multi-round IM) the count of feasible seed sets is
+// C(n, k)^T, so ln C(n, k) becomes T ln C(n, k), and the greedy's guarantee
+// over that partition matroid, 1/2, replaces 1 - 1/e; T = 1 is IMM.
+ImmConst mrim_constants(uint32_t n, uint32_t k, uint32_t T, double eps, double ell) {
   ImmConst c;
   const double logn = std::log((double)n);
   c.ellp = ell * (1.0 + std::log(2.0) / logn);
   c.epsp = std::sqrt(2.0) * eps;
   double lnc = 0.0;
   for (uint32_t i = 0; i < k; ++i) lnc += std::log((double)(n - i)) - std::log((double)(i + 1));
+  lnc *= (double)T;
   c.lam1 = (2.0 + 2.0 * c.epsp / 3.0) * (lnc + c.ellp * logn + std::log(std::log2((double)n))) * (double)n /
            (c.epsp * c.epsp);
-  const double g = 1.0 - std::exp(-1.0);
+  const double g = T == 1 ? 1.0 - std::exp(-1.0) : 0.5;
   const double alpha = std::sqrt(c.ellp * logn + std::log(2.0));
   const double beta = std::sqrt(g * (lnc + c.ellp * logn + std::log(2.0)));
   const double t = g * alpha + beta;
@@ -95,6 +99,8 @@ ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell) {
   c.i_max = (31 - __builtin_clz(n)) - 1;
   return c;
 }
+
+ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell) { return mrim_constants(n, k, 1, eps, ell); }
 
 
 DeviceShared &device_shared(int device) { return g_shared[device]; }
@@ -227,6 +233,9 @@ void fill_desc(InstDesc &d, gim_ctx *c, uint64_t seed, uint64_t item_begin) {
   d.key = PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
   d.j_begin = c->R;
   d.jhi = c->jhi;
+  d.rhi = c->rhi;
+  d.moff = c->moff;
+  d.idoff = c->idoff;
   d.item_begin = item_begin;
   d.store_tail = c->store_used;
   d.members_added = 0;

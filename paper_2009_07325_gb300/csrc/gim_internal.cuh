@@ -145,10 +145,17 @@ struct InstDesc {
   uint64_t *rr_start;
   uint32_t *rr_len;
   uint32_t *cnt;
-  // job: global items [item_begin, item_begin + count) are rr_ids j_begin ...
+  // job: global items [item_begin, item_begin + count) are positions j_begin ...
+  // The set at position j has rr_id (jhi : j + idoff); its root is drawn with
+  // the high word rhi (= jhi except for a multi-round set's later rounds,
+  // which share round 0's root), and its members are stored as moff + v.
   PhiloxKey key;
   unsigned long long j_begin;
   unsigned long long item_begin;
+  uint32_t rhi;
+  uint32_t moff;
+  uint32_t idoff;
+  uint32_t pad1;
   // written by the kernels
   unsigned long long store_tail;     // store entries reserved (starts at the entries already used)
   unsigned long long members_added;  // members of the sets stored by this launch
@@ -273,14 +280,23 @@ struct GreedyDesc {
   unsigned long long *covered_total = nullptr;   // zero on entry
   unsigned long long *stats = nullptr;   // 2, zero on entry: members of newly covered sets, seed list/row words
   unsigned int *bar = nullptr;           // group barrier counter, zero on entry
+  // multi-round IM: elements x in [r * part_n, (r + 1) * part_n) belong to
+  // round r, and at most part_k seeds are taken per round (part_n = 0: no
+  // partition). k is then part_k times the number of rounds.
+  uint32_t part_n = 0, part_k = 0;
 };
 constexpr int kGreedyThreads = 512;
+constexpr uint32_t kMaxRounds = 32;      // rounds of a multi-round collection (one bit each in the greedy)
 // Blocks one cooperative launch of the greedy kernel may use on this device.
 uint32_t greedy_max_blocks(int sm_count);
 // Runs the greedy rounds of d[0..ni) (device array) as one cooperative
 // launch of `grid` blocks. *err (device, zero on entry) becomes nonzero if a
 // group barrier gave up waiting.
-cudaError_t launch_greedy(const GreedyDesc *d, uint32_t ni, uint32_t grid, unsigned int *err, cudaStream_t s);
+// part: some instance has part_n > 0 (multi-round); it must then fit the
+// grid that greedy_max_blocks gives (the multi-round kernel has the same
+// occupancy or better).
+cudaError_t launch_greedy(const GreedyDesc *d, uint32_t ni, uint32_t grid, unsigned int *err, cudaStream_t s,
+                          bool part = false);
 
 // Per-device state shared by every context of the device: sampling scratch
 // and launch tables. Its mutex serialises the sampling of all contexts that
@@ -312,6 +328,13 @@ struct SampleJobH {
   uint64_t count;
 };
 
+// Multi-round RR sets |R| .. |R|+count-1 of ctx's multi-round collection
+// (ctx->rounds > 1): every round sampled through its view in one launch, then
+// merged into the collection in rr_id order.
+gim_status mrim_sample(gim_ctx *ctx, int model, uint64_t seed, uint64_t count);
+// Frees ctx's per-round views and the merge scratch.
+void mrim_release(gim_ctx *ctx);
+
 // IMM constants (Tang, Shi, Xiao 2015): ell', eps', lambda', lambda*, and
 // the number of lower-bound rounds floor(log2 n) - 1.
 struct ImmConst {
@@ -321,6 +344,8 @@ struct ImmConst {
 
 // engine.cu
 ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell);
+// The same for multi-round IM with T rounds of k seeds (T = 1: imm_constants).
+ImmConst mrim_constants(uint32_t n, uint32_t k, uint32_t T, double eps, double ell);
 gim_status set_err(gim_ctx *ctx, gim_status st, const char *fmt, ...);
 gim_status cuda_err(gim_ctx *ctx, cudaError_t e, const char *what);
 gim_status shared_acquire(gim_ctx *ctx);
@@ -360,6 +385,7 @@ struct SelInput {
   const SelectBuffers *index = nullptr;
   uint64_t index_R = 0;
   bool index_only = false;               // build this instance's index only (no greedy rounds)
+  uint32_t part_n = 0, part_k = 0;       // multi-round partition (see GreedyDesc)
 };
 
 // Greedy selection of a fixed set of slots (n, k fixed), one CUDA graph per
@@ -415,6 +441,14 @@ struct gim_ctx {
   int model = -1;
   uint64_t seed = 0;
   uint32_t jhi = 0;   // rr_id of the set at position j is (jhi:j): 2^31 after a fresh final phase, else 0
+  uint32_t rhi = 0;   // high word of the root draw (= jhi; 0 in a multi-round view)
+  uint32_t moff = 0;  // stored member = moff + vertex (t * n in round t's view)
+  uint32_t idoff = 0; // rr_id low word = position + idoff (a view's chunk starts at the parent's |R|)
+  uint32_t rounds = 1;            // T of a multi-round collection; elements t * n + v (1: plain RR sets)
+  uint64_t cnt_cap = 0;           // entries of st.cnt (n * rounds at most)
+  std::vector<gim_ctx *> round_views;   // per-round sampling views of a multi-round collection
+  unsigned long long *mr_tiles = nullptr;   // multi-round merge scratch
+  uint64_t mr_tiles_cap = 0;
   uint64_t R = 0;                 // |R|
   uint64_t Z = 0;                 // members over all stored sets
   uint64_t store_used = 0;        // store entries reserved (>= Z: holes after a store overflow)

@@ -22,6 +22,11 @@
 //           So the hottest counters (hubs sit in a large share of the
 //           sets) see one global atomic per block and round, not one per set.
 //
+// Multi-round IM (part_n > 0): the elements are (vertex, round) pairs in
+// rounds of part_n ids, and a round takes at most part_k seeds. Every block
+// counts the seeds per round as it reads them (best[t] is the same for all
+// blocks) and leaves the elements of full rounds out of its argmax.
+//
 // A group barrier is a counter that every block of the group bumps; a block
 // waits until it reaches the round's target. Every wait is bounded: past the
 // limit the block sets the error flag and the whole group returns, so the
@@ -129,9 +134,31 @@ __device__ __forceinline__ void flush_hubs(int *s_delta, uint32_t *hc, uint32_t 
   }
 }
 
-__global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc *d, uint32_t ni, unsigned int *err) {
+// Largest key over the light counts [x0, x1) and (block 0 of the group) the
+// hub counts, leaving out the elements of rounds whose bit is set in
+// `closed` (round = x / pn; pn = 0: no rounds).
+__device__ __forceinline__ unsigned long long argmax_part(const GreedyDesc &D, uint32_t x0, uint32_t x1, uint32_t H,
+                                                          const uint32_t *hid, const uint32_t *hc, uint32_t lb,
+                                                          uint32_t pn, uint32_t closed) {
+  unsigned long long m = 0;
+#pragma unroll 1
+  for (uint32_t x = x0 + threadIdx.x; x < x1; x += kGreedyThreads)
+    if (!((closed >> (x / pn)) & 1u)) m = umax(m, key_of(__ldcg(D.cnt_work + x), x));
+  if (lb == 0)
+#pragma unroll 1
+    for (uint32_t s = threadIdx.x; s < H; s += kGreedyThreads)
+      if (!((closed >> (hid[s] / pn)) & 1u)) m = umax(m, key_of(__ldcg(hc + s), hid[s]));
+  return m;
+}
+
+// kPart: some instance of the launch is multi-round (part_n > 0). A separate
+// kernel keeps the plain one's code and registers (two blocks per SM).
+template <bool kPart>
+__device__ __forceinline__ void greedy_body(const GreedyDesc *d, uint32_t ni, unsigned int *err) {
   __shared__ unsigned long long part[kGreedyThreads / 32];
   __shared__ int s_delta[kHeavyCap];
+  __shared__ uint32_t s_picks[kMaxRounds];
+  __shared__ uint32_t s_closed;
   uint32_t lo = 0, hi = ni - 1;
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
@@ -146,6 +173,10 @@ __global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc
   const uint32_t nb = D.g_blocks, n = D.n;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   for (uint32_t s = threadIdx.x; s < kHeavyCap; s += kGreedyThreads) s_delta[s] = 0;
+  if (threadIdx.x < kMaxRounds) s_picks[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_closed = 0;
+  const uint32_t pn = kPart ? D.part_n : 0u;
+  __syncthreads();
   const uint32_t H = D.hmeta[0] < kHeavyCap ? D.hmeta[0] : kHeavyCap;   // written before this launch
   const uint32_t *hid = D.hmeta + 1;
   uint32_t *hc = D.hmeta + 1 + kHeavyCap;
@@ -166,14 +197,19 @@ __global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc
   for (uint32_t t = 0; t < D.k; ++t) {
     // argmax (counts change between rounds: read them at L2)
     unsigned long long m = 0;
+    if (pn) {
+      m = argmax_part(D, x0, x1, H, hid, hc, lb, pn, s_closed);
+    } else {
 #pragma unroll 4
-    for (uint32_t x = x0 + 4 * threadIdx.x; x < x1v; x += 4 * kGreedyThreads) {
-      const uint4 c = __ldcg(cw4 + (x >> 2));
-      m = umax(m, umax(umax(key_of(c.x, x), key_of(c.y, x + 1)), umax(key_of(c.z, x + 2), key_of(c.w, x + 3))));
+      for (uint32_t x = x0 + 4 * threadIdx.x; x < x1v; x += 4 * kGreedyThreads) {
+        const uint4 c = __ldcg(cw4 + (x >> 2));
+        m = umax(m, umax(umax(key_of(c.x, x), key_of(c.y, x + 1)), umax(key_of(c.z, x + 2), key_of(c.w, x + 3))));
+      }
+      for (uint32_t x = x1v + threadIdx.x; x < x1; x += kGreedyThreads)
+        m = umax(m, key_of(__ldcg(D.cnt_work + x), x));
+      if (lb == 0)
+        for (uint32_t s = threadIdx.x; s < H; s += kGreedyThreads) m = umax(m, key_of(__ldcg(hc + s), hid[s]));
     }
-    for (uint32_t x = x1v + threadIdx.x; x < x1; x += kGreedyThreads) m = umax(m, key_of(__ldcg(D.cnt_work + x), x));
-    if (lb == 0)
-      for (uint32_t s = threadIdx.x; s < H; s += kGreedyThreads) m = umax(m, key_of(__ldcg(hc + s), hid[s]));
     m = warp_max(m);
     if (lane == 0) part[wib] = m;
     __syncthreads();
@@ -189,6 +225,10 @@ __global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc
     const uint32_t u = ~(uint32_t)(key & 0xFFFFFFFFull);
     const uint32_t cw = (uint32_t)(key >> 32);
     const uint32_t us = D.hslot[u];
+    if (pn && threadIdx.x == 0) {   // this round's seed counts toward its round (read by the next argmax)
+      const uint32_t r = u / pn;
+      if (r < kMaxRounds && ++s_picks[r] == D.part_k) s_closed |= 1u << r;
+    }
     if (lb == 0 && threadIdx.x == 0) {
       D.seeds[t] = u;
       D.gains[t] = cw ? cw - 1u : 0u;
@@ -271,6 +311,16 @@ __global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc
   }
 }
 
+__global__ void __launch_bounds__(kGreedyThreads) greedy_kernel(const GreedyDesc *d, uint32_t ni, unsigned int *err) {
+  greedy_body<false>(d, ni, err);
+}
+
+// at most 64 registers, so that it fits the grid sized for greedy_kernel
+__global__ void __launch_bounds__(kGreedyThreads, 2) greedy_part_kernel(const GreedyDesc *d, uint32_t ni,
+                                                                          unsigned int *err) {
+  greedy_body<true>(d, ni, err);
+}
+
 }  // namespace
 
 uint32_t greedy_max_blocks(int sm_count) {
@@ -284,10 +334,12 @@ uint32_t greedy_max_blocks(int sm_count) {
   return (uint32_t)std::max(1, std::min(per_sm, 2) * sm_count);
 }
 
-cudaError_t launch_greedy(const GreedyDesc *d, uint32_t ni, uint32_t grid, unsigned int *err, cudaStream_t s) {
+cudaError_t launch_greedy(const GreedyDesc *d, uint32_t ni, uint32_t grid, unsigned int *err, cudaStream_t s,
+                          bool part) {
   if (grid == 0 || ni == 0) return cudaSuccess;
   void *args[] = {(void *)&d, (void *)&ni, (void *)&err};
-  return cudaLaunchCooperativeKernel((const void *)greedy_kernel, dim3(grid), dim3(kGreedyThreads), args, 0, s);
+  const void *fn = part ? (const void *)greedy_part_kernel : (const void *)greedy_kernel;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGreedyThreads), args, 0, s);
 }
 
 }  // namespace gim

@@ -83,13 +83,19 @@ struct InstView {
   uint32_t *cnt;
   PhiloxKey key;
   unsigned long long j_begin;
-  uint32_t jhi;   // the rr_id of the set at position j is (jhi:j); positions stay below 2^32
+  uint32_t jhi;    // the rr_id of the set at position j is (jhi : j + idoff); positions stay below 2^32
+  uint32_t rhi;    // high word of the root draw
+  uint32_t moff;   // stored member = moff + vertex
+  uint32_t idoff;
 };
 
 __device__ __forceinline__ InstView view_of(const InstDesc &d) {
   return InstView{d.n, d.off, d.src, d.thr, d.rthr, d.rw, d.cum, d.members, d.store_cap, d.rr_start, d.rr_len, d.cnt,
-                  d.key, d.j_begin, d.jhi};
+                  d.key, d.j_begin, d.jhi, d.rhi, d.moff, d.idoff};
 }
+
+// Low word of the rr_id of the set at position j.
+__device__ __forceinline__ uint32_t id_lo(const InstView &V, uint64_t j) { return (uint32_t)j + V.idoff; }
 
 // Instance and rr_id of work item `item`, and the instance's view.
 template <bool kOne>
@@ -128,8 +134,8 @@ __device__ __forceinline__ void commit_warp(const SampleLaunch &L, const InstVie
   for (uint32_t i = lane; i < size; i += 32) {
     const uint32_t x = q[i];
     if (fits) {
-      members[base + i] = x;
-      atomicAdd(&cnt[x], 1u);
+      members[base + i] = V.moff + x;
+      atomicAdd(&cnt[V.moff + x], 1u);
     }
     if (bm) bm[x >> 5] = 0u;   // every set bit of the bitmap belongs to this set
   }
@@ -301,14 +307,14 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
     const uint32_t *__restrict__ thr = V.thr;
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
-    const CoinKey ck = coin_key((uint32_t)j, V.jhi, key);
+    const CoinKey ck = coin_key(id_lo(V, j), V.jhi, key);
 
     if (++epoch == 0xFFFFFFFFu) {              // epochs ran out: wipe the table once
       for (uint32_t h = lane; h < kHashSlots; h += 32) ht[h] = 0ull;
       __syncwarp();
       epoch = 1;
     }
-    const uint32_t root = draw_root(key, (uint32_t)j, V.jhi, V.n);
+    const uint32_t root = draw_root(key, id_lo(V, j), V.rhi, V.n);
     if (lane == 0) {
       q[0] = root;
       ht[(root * 0x9E3779B1u) >> (32 - kHashBits)] = ((unsigned long long)epoch << 32) | root;
@@ -434,9 +440,9 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
     const uint32_t *__restrict__ thr = V.thr;
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
-    const CoinKey ck = coin_key((uint32_t)j, V.jhi, key);
+    const CoinKey ck = coin_key(id_lo(V, j), V.jhi, key);
     if (tid == 0) {
-      const uint32_t root = draw_root(key, (uint32_t)j, V.jhi, V.n);
+      const uint32_t root = draw_root(key, id_lo(V, j), V.rhi, V.n);
       q[0] = root;
       bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
       s_head = 0;
@@ -542,8 +548,8 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
     for (uint32_t i = tid; i < size; i += kBigBlock) {
       const uint32_t x = q[i];
       if (fits) {
-        V.members[base + i] = x;
-        atomicAdd(&V.cnt[x], 1u);
+        V.members[base + i] = V.moff + x;
+        atomicAdd(&V.cnt[V.moff + x], 1u);
       }
       bm[x >> 5] = 0u;
     }
@@ -655,8 +661,8 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     const uint32_t *__restrict__ src = V.src;
     const uint32_t *__restrict__ rw = V.rw;
     const PhiloxKey key = V.key;
-    const uint32_t jlo = (uint32_t)j, jhi = V.jhi;
-    uint32_t x = draw_root(key, (uint32_t)j, V.jhi, V.n);
+    const uint32_t jlo = id_lo(V, j), jhi = V.jhi;
+    uint32_t x = draw_root(key, id_lo(V, j), V.rhi, V.n);
     if (lane == 0) {
       path[0] = x;
       if (kLarge) bm[x >> 5] = 1u << (x & 31u);
@@ -742,7 +748,7 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
       } else {
         decode_item(L, item, ii, j);
         V = view_of(L.inst[ii]);
-        x = draw_root(V.key, (uint32_t)j, V.jhi, V.n);
+        x = draw_root(V.key, id_lo(V, j), V.rhi, V.n);
         if (gl == 0) path[0] = x;
         len = 1;
         active = true;
@@ -758,7 +764,7 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
       s = V.off[x];
       e = V.off[x + 1];
       wb = V.rw[x];
-      U = philox10(x, kTagStep, (uint32_t)j, V.jhi, V.key).x;
+      U = philox10(x, kTagStep, id_lo(V, j), V.jhi, V.key).x;
       if (e == s) ended = true;
     }
     // window of eight thresholds around the guess (rows of equal weights)
@@ -867,7 +873,7 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
       const bool fits = base + len <= V.store_cap;
       if (fits)
         for (uint32_t i = gl; i < len; i += kLtLanes) {
-          const uint32_t m = path[i];
+          const uint32_t m = V.moff + path[i];
           V.members[base + i] = m;
           atomicAdd(&V.cnt[m], 1u);
         }

@@ -60,7 +60,8 @@ gim_status autotune(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *par
           ctxs[i]->group_budget = cand;
           ctxs[i]->R = ctxs[i]->Z = ctxs[i]->store_used = 0;
           ctxs[i]->model = -1;
-          ctxs[i]->jhi = 0;
+          ctxs[i]->jhi = ctxs[i]->rhi = 0;
+          ctxs[i]->rounds = 1;
           const cudaError_t e = cudaMemsetAsync(ctxs[i]->st.cnt, 0, (uint64_t)ctxs[i]->g.n * 4, ctx->stream);
           if (e != cudaSuccess) return cuda_err(ctx, e, "autotune reset");
         }
@@ -84,7 +85,8 @@ gim_status autotune(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *par
     ctxs[i]->group_budget = best;
     ctxs[i]->R = ctxs[i]->Z = ctxs[i]->store_used = 0;
     ctxs[i]->model = -1;
-    ctxs[i]->jhi = 0;
+    ctxs[i]->jhi = ctxs[i]->rhi = 0;
+    ctxs[i]->rounds = 1;
     const cudaError_t e = cudaMemsetAsync(ctxs[i]->st.cnt, 0, (uint64_t)ctxs[i]->g.n * 4, ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "autotune reset");
   }
