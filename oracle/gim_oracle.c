@@ -15,7 +15,9 @@
  *    tag 0 = root draw (idx 0, 64-bit word w1:w0, root = high half of
  *    word * n); tag 1 = IC coin of in-edge e (idx e/4, word e%4);
  *    tag 2 = LT draw at vertex x (idx x, word 0).
- *  - IC coin: edge e is live iff float(word >> 8) * 2^-24 < w[e] (fp32).
+ *  - IC coin: edge e is live iff float(word >> 8) * 2^-24 < w[e] (fp32);
+ *    for w[e] <= 2^-8 the 24-bit uniform is drawn as a zero-test byte (16
+ *    per draw) and a 16-bit residual (see orc_ic_live).
  *  - LT thresholds: cum[e_i] = min(2^32, llround(P_i * 2^32)) with P_i the
  *    fp64 running sum of the row's weights in CSR order; a row whose total
  *    is within 1e-6 of 1 has its last threshold set to 2^32.
@@ -81,13 +83,32 @@ uint32_t orc_root(uint64_t seed, uint64_t j, uint32_t n) {
   return (uint32_t)(((unsigned __int128)r * n) >> 64);
 }
 
-/* The coin of Alg. 3 ("p = U(0,1)", "p < p_uv") for in-edge e of RR set j. */
+/*
+ * The coin of Alg. 3 ("p = U(0,1)", "p < p_uv") for in-edge e of RR set j.
+ * Edges with p > 2^-8: u = word (e mod 4) of draw (tag 1, idx e/4), reduced
+ * to its top 24 bits, live iff u 2^-24 < p. Edges with p <= 2^-8 draw the
+ * same 24-bit uniform in two independent parts: its top 8 bits are byte
+ * (e mod 16) of draw (tag 1, idx 2^31 + e/16) and must be zero (otherwise
+ * u >= 2^-8 >= p), and its low 16 bits h are half-word (e mod 8) of draw
+ * (tag 1, idx 2^30 + e/8); then live iff h 2^-24 < p. Both give
+ * Pr[live] = ceil(p 2^24) / 2^24, independently per edge; the second form
+ * spends one draw per 16 edges where almost every edge is dead. The three
+ * idx ranges are disjoint for e < 2^32.
+ */
 int orc_ic_live(uint64_t seed, uint64_t j, uint64_t e, float p) {
   uint32_t w[4];
-  draw4(seed, j, 1, (uint32_t)(e >> 2), w);
-  uint32_t word = w[e & 3];
-  float u = (float)(word >> 8) * 0x1p-24f;
-  return u < p;
+  if (p > 0x1p-8f) {
+    draw4(seed, j, 1, (uint32_t)(e >> 2), w);
+    uint32_t word = w[e & 3];
+    float u = (float)(word >> 8) * 0x1p-24f;
+    return u < p;
+  }
+  draw4(seed, j, 1, 0x80000000u | (uint32_t)(e >> 4), w);
+  const uint32_t top = (w[(e >> 2) & 3] >> (8 * (e & 3))) & 0xFFu;
+  if (top != 0) return 0;
+  draw4(seed, j, 1, 0x40000000u | (uint32_t)(e >> 3), w);
+  const uint32_t h = (w[(e >> 1) & 3] >> (16 * (e & 1))) & 0xFFFFu;
+  return (float)h * 0x1p-24f < p;
 }
 
 /* The single uniform drawn at vertex x of an LT walk (Sec. III-G). */
