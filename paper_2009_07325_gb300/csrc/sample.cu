@@ -15,7 +15,12 @@
 //   lane per step, one Philox call giving a group's four coin words. A row
 //   whose in-edges share one probability (weighted cascade, uniform p) uses
 //   its common threshold, so the scan reads no edge data; otherwise one
-//   16-byte load fetches a group's four thresholds. Live edges are buffered
+//   16-byte load fetches a group's four thresholds. A row whose common
+//   probability is at most 2^-8 (the hub rows of weighted cascade, where
+//   almost all coin work lies) is scanned in super-groups of 16 in-edges:
+//   one Philox call gives the top bytes of 16 coin uniforms, and only an
+//   edge whose byte is zero (1 in 256) draws its low 16 bits (sgroup_live).
+//   Live edges are buffered
 //   in shared memory and resolved 32 per round trip: read the source,
 //   insert it into the worker's visited hash set, append the newly visited
 //   to the worker's queue (which doubles as the member list: Sec. III-A,
@@ -24,7 +29,8 @@
 //   more than its edge budget is abandoned and deferred.
 // IC, large-set pass: one 256-thread block per deferred set, with an n-bit
 //   visited bitmap and a queue. Each batch of up to 512 frontier
-//   vertices is cut into chunks of at most 2048 in-edges that the block's
+//   vertices is cut into chunks of at most 512 Philox calls (2048 in-edges,
+//   or 8192 in a super-group row) that the block's
 //   warps take from a shared counter, so the heavy tail of huge RR sets is
 //   spread over 8 warps. Only __syncthreads barriers are used.
 // LT: the reverse walk of Sec. III-G (four walks per warp in the common pass, see
@@ -155,25 +161,92 @@ __device__ __forceinline__ void commit_warp(const SampleLaunch &L, const InstVie
 // word <= t * 256 - 1; lim() gives that bound (t = 0 rows are never scanned).
 __device__ __forceinline__ uint32_t lim(uint32_t t) { return (t << 8) - 1u; }
 
+// Coins of in-edges with threshold t <= 2^16 (p <= 2^-8): the edge's 24-bit
+// uniform is drawn as its top byte, byte e mod 16 of the words of group
+// kScreenIdx + e/16 (almost always nonzero: dead), and, only when that byte
+// is zero, its low 16 bits, half-word e mod 8 of group kResidIdx + e/8; then
+// live iff those bits < t. The coin probability is t / 2^24 as for the
+// one-word coin, and one Philox call settles 16 edges instead of 4.
+constexpr uint32_t kScreenMax = 1u << 16;
+constexpr uint32_t kScreenIdx = 0x80000000u;   // group indices of the top bytes
+constexpr uint32_t kResidIdx = 0x40000000u;    // group indices of the residuals (one-word groups stay below 2^30)
+__device__ __forceinline__ bool screened(uint32_t t) { return t - 1u < kScreenMax; }   // 1 <= t <= 2^16
+
+// Bit i of the result is set iff byte i of x is zero (exact per byte).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
+  const uint32_t t = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);   // 0x80 in each zero byte
+  return ((t >> 7) & 1u) | ((t >> 14) & 2u) | ((t >> 21) & 4u) | ((t >> 28) & 8u);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &r, uint32_t i) {
+  return i == 0 ? r.x : i == 1 ? r.y : i == 2 ? r.z : r.w;
+}
+
+// Second part of a screened coin: the 16-bit residual of in-edge x against t.
+__device__ __forceinline__ bool resid_live(uint32_t x, uint32_t t, const CoinKey &ck) {
+  const uint4 h = coin_words(kResidIdx | (x >> 3), ck);
+  return ((word_of(h, (x >> 1) & 3u) >> ((x & 1u) << 4)) & 0xFFFFu) < t;
+}
+
+// Coins of super-group sg (in-edges 16sg .. 16sg+15) of the row [s, e) whose
+// common threshold rt is screened: bit i is set iff edge 16sg+i lies in the
+// row and is live.
+__device__ __forceinline__ uint32_t sgroup_live(uint32_t sg, uint32_t s, uint32_t e, uint32_t rt, const CoinKey &ck) {
+  const uint4 r = coin_words(kScreenIdx | sg, ck);
+  const uint32_t any = ((r.x - 0x01010101u) & ~r.x) | ((r.y - 0x01010101u) & ~r.y) | ((r.z - 0x01010101u) & ~r.z) |
+                       ((r.w - 0x01010101u) & ~r.w);
+  if ((any & 0x80808080u) == 0u) return 0u;   // no zero byte (about 94 % of super-groups)
+  uint32_t z = zero_bytes(r.x) | (zero_bytes(r.y) << 4) | (zero_bytes(r.z) << 8) | (zero_bytes(r.w) << 12);
+  const uint32_t e0 = sg << 4;                // s - 15 <= e0 <= e - 1
+  if (e0 < s || e0 + 16 > e) {
+    const uint32_t lo = s > e0 ? s - e0 : 0u;
+    const uint32_t hi = e - e0 < 16u ? e - e0 : 16u;
+    z &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+  }
+  uint32_t live = 0;
+  while (z) {
+    const uint32_t i = __ffs(z) - 1;
+    z &= z - 1;
+    if (resid_live(e0 + i, rt, ck)) live |= 1u << i;
+  }
+  return live;
+}
+
 // Coins of group grp (in-edges 4grp .. 4grp+3) for the row [s, e): bit qi is
 // set iff edge 4grp+qi lies in the row and is live. One Philox call yields
 // the four coin words. The threshold is the row's common one when it has
-// one (rt != kPerEdge; rl = lim(rt)), so the scan of such a row touches no
-// memory; there the usual answer (no live edge: all four words above the
-// bound) is settled by their minimum.
+// one (rt != kPerEdge; rl = lim(rt); never a screened one: such rows go
+// through sgroup_live), so the scan of such a row touches no memory; there
+// the usual answer (no live edge: all four words above the bound) is
+// settled by their minimum. With per-edge thresholds, screened edges take
+// their top byte from word grp mod 4 of their super-group's draw.
 __device__ __forceinline__ uint32_t group_live(const uint32_t *__restrict__ thr, uint32_t grp, uint32_t s, uint32_t e,
                                                uint32_t rt, uint32_t rl, const CoinKey &ck) {
-  const uint4 r = coin_words(grp, ck);
   uint32_t live;
   if (rt != kPerEdge) {
+    const uint4 r = coin_words(grp, ck);
     if (min(min(r.x, r.y), min(r.z, r.w)) > rl) return 0u;
     live = (r.x <= rl ? 1u : 0u) | (r.y <= rl ? 2u : 0u) | (r.z <= rl ? 4u : 0u) | (r.w <= rl ? 8u : 0u);
   } else {
     const uint4 tv = reinterpret_cast<const uint4 *>(thr)[grp];
     // a zero threshold never fires; lim(0) wraps, so such edges are masked out
     const uint32_t nz = (tv.x ? 1u : 0u) | (tv.y ? 2u : 0u) | (tv.z ? 4u : 0u) | (tv.w ? 8u : 0u);
-    live = ((r.x <= lim(tv.x) ? 1u : 0u) | (r.y <= lim(tv.y) ? 2u : 0u) | (r.z <= lim(tv.z) ? 4u : 0u) |
-            (r.w <= lim(tv.w) ? 8u : 0u)) & nz;
+    const uint32_t sc = (screened(tv.x) ? 1u : 0u) | (screened(tv.y) ? 2u : 0u) | (screened(tv.z) ? 4u : 0u) |
+                        (screened(tv.w) ? 8u : 0u);
+    live = 0u;
+    if ((nz & ~sc) != 0u) {
+      const uint4 r = coin_words(grp, ck);
+      live = ((r.x <= lim(tv.x) ? 1u : 0u) | (r.y <= lim(tv.y) ? 2u : 0u) | (r.z <= lim(tv.z) ? 4u : 0u) |
+              (r.w <= lim(tv.w) ? 8u : 0u)) & nz & ~sc;
+    }
+    if (sc) {
+      uint32_t z = zero_bytes(word_of(coin_words(kScreenIdx | (grp >> 2), ck), grp & 3u)) & sc;
+      while (z) {
+        const uint32_t qi = __ffs(z) - 1;
+        z &= z - 1;
+        if (resid_live((grp << 2) + qi, word_of(tv, qi), ck)) live |= 1u << qi;
+      }
+    }
   }
   const uint32_t e0 = grp << 2;            // s - 3 <= e0 <= e - 1
   if (e0 < s || e0 + 4 > e) {
@@ -219,6 +292,28 @@ __device__ __forceinline__ uint32_t step_live(const uint32_t *__restrict__ thr, 
   return n;
 }
 
+// Super-group coins of one warp step over [base, base + kStepGroups) of a
+// screened row whose last super-group is glast; lv[q] holds lane super-group
+// base + 32q + lane.
+__device__ __forceinline__ void step_live_sg(uint32_t base, uint32_t glast, uint32_t s, uint32_t e, uint32_t rt,
+                                             const CoinKey &ck, uint32_t (&lv)[kGPL]) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (uint32_t q = 0; q < kGPL; ++q) {
+    const uint32_t g = base + 32 * q + lane;
+    lv[q] = g <= glast ? sgroup_live(g, s, e, rt, ck) : 0u;
+  }
+}
+
+// Appends the live edges of super-group sg (mask m) to cand, starting at pos.
+__device__ __forceinline__ void push_live_sg(uint32_t *cand, uint32_t pos, uint32_t sg, uint32_t m) {
+  while (m) {
+    const uint32_t i = __ffs(m) - 1;
+    m &= m - 1;
+    cand[pos++] = (sg << 4) + i;
+  }
+}
+
 // Appends the live edges of one warp step to cand, starting at pos.
 __device__ __forceinline__ void push_live(uint32_t *cand, uint32_t pos, uint32_t base, const uint32_t (&lv)[kGPL]) {
   const uint32_t lane = lane_id();
@@ -231,6 +326,7 @@ __device__ __forceinline__ void push_live(uint32_t *cand, uint32_t pos, uint32_t
 
 constexpr uint32_t kCandCap = 512;   // per-warp buffer of live edges awaiting their visited test
 static_assert(kCandCap >= 128 * kGPL, "one warp step's live edges fit the buffer");
+static_assert(kCandCap >= 16 * 32, "one super-group per lane's live edges fit the buffer");
 
 // Visited set of the common pass: open addressing over kHashSlots 64-bit
 // slots holding epoch << 32 | vertex; a slot whose epoch is not the current
@@ -341,6 +437,28 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         const uint32_t s = __shfl_sync(kFullMask, rs, b), e = __shfl_sync(kFullMask, re, b);
         const uint32_t rt = __shfl_sync(kFullMask, rr, b);
         if (e <= s || rt == 0u) continue;      // a row whose coins are all 0 adds nothing
+        if (screened(rt)) {                    // 16 coins per Philox call
+          const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
+          scanned += 4 * (g1 - g0 + 1);
+          for (uint32_t base = g0; base <= g1 && !overflow; base += kStepGroups) {
+            uint32_t lv[kGPL];
+            step_live_sg(base, g1, s, e, rt, ck, lv);
+#pragma unroll
+            for (uint32_t qq = 0; qq < kGPL; ++qq) {
+              const uint32_t mine = __popc(lv[qq]);
+              if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
+              uint32_t total;
+              const uint32_t excl = warp_excl(mine, total);   // at most 16 * 32 = kCandCap
+              if (ncand + total > kCandCap) {
+                common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
+                ncand = 0;
+              }
+              push_live_sg(cand, ncand + excl, base + 32 * qq + lane, lv[qq]);
+              ncand += total;
+            }
+          }
+          continue;
+        }
         const uint32_t rl = lim(rt);
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
         scanned += g1 - g0 + 1;
@@ -377,7 +495,8 @@ constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices p
 constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr int kBigBlocksPerSM = 8;          // register cap that keeps 8 blocks (64 warps) per SM
-constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
+constexpr uint32_t kBigCand = 512;           // per-warp candidate buffer: one warp step's live edges at most
+static_assert(kBigCand >= 128 * kGPL && kBigCand >= 16 * 32, "a step (or a super-group per lane) fits the buffer");
 static_assert(kChunkGroups % kStepGroups == 0, "a chunk is whole warp steps");
 
 // Resolves a warp's buffered live edges: a source not yet in the set joins
@@ -465,7 +584,9 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
           b_s[b] = s;
           b_e[b] = e;
           b_rt[b] = rt;
-          nch[r] = (e > s && rt != 0u) ? (((e - 1) >> 2) - (s >> 2) + kChunkGroups) / kChunkGroups : 0u;
+          // a chunk is kChunkGroups Philox calls: groups of 4 in-edges, or super-groups of 16
+          const uint32_t sh = screened(rt) ? 4u : 2u;
+          nch[r] = (e > s && rt != 0u) ? (((e - 1) >> sh) - (s >> sh) + kChunkGroups) / kChunkGroups : 0u;
         }
         mine += nch[r];
       }
@@ -504,6 +625,29 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
             hi = mid - 1;
         }
         const uint32_t s = b_s[lo], e = b_e[lo], rt = b_rt[lo], rl = lim(rt);
+        if (screened(rt)) {
+          const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
+          const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkGroups;
+          const uint32_t c1 = c0 + kChunkGroups - 1 < g1 ? c0 + kChunkGroups - 1 : g1;
+          for (uint32_t base = c0; base <= c1; base += kStepGroups) {
+            uint32_t lv[kGPL];
+            step_live_sg(base, c1, s, e, rt, ck, lv);
+#pragma unroll
+            for (uint32_t qq = 0; qq < kGPL; ++qq) {
+              const uint32_t mine = __popc(lv[qq]);
+              if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
+              uint32_t total;
+              const uint32_t excl = warp_excl(mine, total);
+              if (ncand + total > kBigCand) {
+                block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
+                ncand = 0;
+              }
+              push_live_sg(cand, ncand + excl, base + 32 * qq + lane, lv[qq]);
+              ncand += total;
+            }
+          }
+          continue;
+        }
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
         const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkGroups;
         const uint32_t c1 = c0 + kChunkGroups - 1 < g1 ? c0 + kChunkGroups - 1 : g1;

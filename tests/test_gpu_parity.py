@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context, GimError
+from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context, GimError, binding
 from paper_2009_07325_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -188,6 +188,35 @@ def test_sets_beyond_the_capped_queue():
     off, _ = orc.export()
     assert np.diff(off).min() > (1 << 20)
     _same_collection(ctx, orc)
+
+
+@pytest.mark.parametrize("budget", [0, 1])
+def test_screened_coins_bit_exact(budget):
+    """In-edges with p <= 2^-8 (16 coins per Philox call, residual draws for
+    zero bytes): common-probability rows (a complete fan-in graph, weighted
+    cascade 1/1000) and rows whose per-edge weights straddle 2^-8
+    (log-uniform in [2^-12, 2^-3]); budget 1 sends every set to the
+    block-per-set pass."""
+    K, S = 2000, 1000
+    fan = I.wc_weights(I.from_edges(K + S, np.tile(np.arange(K, K + S, dtype=np.uint32), K),
+                                    np.repeat(np.arange(K, dtype=np.uint32), S), "fanin"))
+    base = I.er(3000, 90000, 21)
+    r = I.u64_stream(21, 5, base.m)
+    w = np.exp2(-3.0 - 9.0 * (r >> np.uint64(11)).astype(np.float64) * 2.0 ** -53).astype(np.float32)
+    mixed = base.with_weights(w, "mixed")
+    for g in (fan, mixed):
+        ctx = _ctx(g)
+        if budget:
+            ctx.set_option(binding.GIM_OPT_GROUP_BUDGET, budget)
+        orc = O.Oracle(g)
+        for count in (7000, 13000):
+            ctx.sample_rr(GIM_IC, count, 9)
+            orc.sample(GIM_IC, 9, count, THREADS)
+        _same_collection(ctx, orc)
+        gs, gg, gc = ctx.select_seeds(20)
+        os_, og, oc = orc.greedy(20)
+        assert gs.tolist() == os_.tolist() and gg.tolist() == og.tolist() and gc == oc
+        ctx.close()
 
 
 def test_degenerate_weights_and_sizes():
