@@ -225,9 +225,11 @@ __device__ __forceinline__ void greedy_body(const GreedyDesc *d, uint32_t ni, un
     const uint32_t u = ~(uint32_t)(key & 0xFFFFFFFFull);
     const uint32_t cw = (uint32_t)(key >> 32);
     const uint32_t us = D.hslot[u];
-    if (pn && threadIdx.x == 0) {   // this round's seed counts toward its round (read by the next argmax)
-      const uint32_t r = u / pn;
-      if (r < kMaxRounds && ++s_picks[r] == D.part_k) s_closed |= 1u << r;
+    if constexpr (kPart) {
+      if (pn && threadIdx.x == 0) {   // this round's seed counts toward its round (read by the next argmax)
+        const uint32_t r = u / pn;
+        if (r < kMaxRounds && ++s_picks[r] == D.part_k) s_closed |= 1u << r;
+      }
     }
     if (lb == 0 && threadIdx.x == 0) {
       D.seeds[t] = u;

@@ -19,7 +19,8 @@
 //   probability is at most 2^-8 (the hub rows of weighted cascade, where
 //   almost all coin work lies) is scanned in super-groups of 16 in-edges:
 //   one Philox call gives the top bytes of 16 coin uniforms, and only an
-//   edge whose byte is zero (1 in 256) draws its low 16 bits (sgroup_live).
+//   edge whose byte is zero (1 in 256) draws its low 16 bits, 32 such edges
+//   at a time from a per-warp pending list (sgroup_zero, resolve_pending).
 //   Live edges are buffered
 //   in shared memory and resolved 32 per round trip: read the source,
 //   insert it into the worker's visited hash set, append the newly visited
@@ -188,14 +189,11 @@ __device__ __forceinline__ bool resid_live(uint32_t x, uint32_t t, const CoinKey
   return ((word_of(h, (x >> 1) & 3u) >> ((x & 1u) << 4)) & 0xFFFFu) < t;
 }
 
-// Coins of super-group sg (in-edges 16sg .. 16sg+15) of the row [s, e) whose
-// common threshold rt is screened: bit i is set iff edge 16sg+i lies in the
-// row and is live.
-__device__ __forceinline__ uint32_t sgroup_live(uint32_t sg, uint32_t s, uint32_t e, uint32_t rt, const CoinKey &ck) {
+// First part of the coins of super-group sg (in-edges 16sg .. 16sg+15) of
+// the row [s, e): bit i is set iff edge 16sg+i lies in the row and its top
+// byte is zero, i.e. its coin depends on its residual (resid_live).
+__device__ __forceinline__ uint32_t sgroup_zero(uint32_t sg, uint32_t s, uint32_t e, const CoinKey &ck) {
   const uint4 r = coin_words(kScreenIdx | sg, ck);
-  const uint32_t any = ((r.x - 0x01010101u) & ~r.x) | ((r.y - 0x01010101u) & ~r.y) | ((r.z - 0x01010101u) & ~r.z) |
-                       ((r.w - 0x01010101u) & ~r.w);
-  if ((any & 0x80808080u) == 0u) return 0u;   // no zero byte (about 94 % of super-groups)
   uint32_t z = zero_bytes(r.x) | (zero_bytes(r.y) << 4) | (zero_bytes(r.z) << 8) | (zero_bytes(r.w) << 12);
   const uint32_t e0 = sg << 4;                // s - 15 <= e0 <= e - 1
   if (e0 < s || e0 + 16 > e) {
@@ -203,20 +201,14 @@ __device__ __forceinline__ uint32_t sgroup_live(uint32_t sg, uint32_t s, uint32_
     const uint32_t hi = e - e0 < 16u ? e - e0 : 16u;
     z &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
   }
-  uint32_t live = 0;
-  while (z) {
-    const uint32_t i = __ffs(z) - 1;
-    z &= z - 1;
-    if (resid_live(e0 + i, rt, ck)) live |= 1u << i;
-  }
-  return live;
+  return z;
 }
 
 // Coins of group grp (in-edges 4grp .. 4grp+3) for the row [s, e): bit qi is
 // set iff edge 4grp+qi lies in the row and is live. One Philox call yields
 // the four coin words. The threshold is the row's common one when it has
 // one (rt != kPerEdge; rl = lim(rt); never a screened one: such rows go
-// through sgroup_live), so the scan of such a row touches no memory; there
+// through sgroup_zero), so the scan of such a row touches no memory; there
 // the usual answer (no live edge: all four words above the bound) is
 // settled by their minimum. With per-edge thresholds, screened edges take
 // their top byte from word grp mod 4 of their super-group's draw.
@@ -274,6 +266,9 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t mine, uint32_t &total) {
 // independent Philox chains are in flight per lane.
 constexpr uint32_t kGPL = 2;
 constexpr uint32_t kStepGroups = 32 * kGPL;
+// Super-groups (of 16 in-edges) each lane scans per warp step in a screened row.
+constexpr uint32_t kSGPL = 2;
+constexpr uint32_t kStepSG = 32 * kSGPL;
 
 // Coins of one warp step over groups [base, base + kStepGroups) of the row
 // [s, e) whose last group is glast; lv[q] holds lane group base + 32q + lane.
@@ -292,25 +287,103 @@ __device__ __forceinline__ uint32_t step_live(const uint32_t *__restrict__ thr, 
   return n;
 }
 
-// Super-group coins of one warp step over [base, base + kStepGroups) of a
-// screened row whose last super-group is glast; lv[q] holds lane super-group
-// base + 32q + lane.
-__device__ __forceinline__ void step_live_sg(uint32_t base, uint32_t glast, uint32_t s, uint32_t e, uint32_t rt,
-                                             const CoinKey &ck, uint32_t (&lv)[kGPL]) {
+// Edges whose top byte was zero wait in a per-warp list with their
+// thresholds until 32 or more can be settled together: one converged round
+// of residual draws per 32 edges, instead of a round (with one or two active
+// lanes) in almost every warp step.
+constexpr uint32_t kPend = 64;
+
+// Settles the pending edges pe/pt[0 .. npend): the live ones go to cand
+// (flush() empties cand when it is full; ncand is its fill).
+template <typename Flush>
+__device__ __forceinline__ void resolve_pending(const uint32_t *pe, const uint32_t *pt, uint32_t &npend, uint32_t *cand,
+                                                uint32_t &ncand, uint32_t cap, const CoinKey &ck, Flush &&flush) {
   const uint32_t lane = lane_id();
-#pragma unroll
-  for (uint32_t q = 0; q < kGPL; ++q) {
-    const uint32_t g = base + 32 * q + lane;
-    lv[q] = g <= glast ? sgroup_live(g, s, e, rt, ck) : 0u;
+  __syncwarp();
+  for (uint32_t i0 = 0; i0 < npend; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    uint32_t x = 0;
+    bool live = false;
+    if (i < npend) {
+      x = pe[i];
+      live = resid_live(x, pt[i], ck);
+    }
+    const uint32_t lm = __ballot_sync(kFullMask, live);
+    if (!lm) continue;
+    const uint32_t n = __popc(lm);
+    if (ncand + n > cap) {
+      flush();
+      ncand = 0;
+    }
+    if (live) cand[ncand + __popc(lm & ((1u << lane) - 1u))] = x;
+    ncand += n;
   }
+  npend = 0;
+  __syncwarp();
 }
 
-// Appends the live edges of super-group sg (mask m) to cand, starting at pos.
-__device__ __forceinline__ void push_live_sg(uint32_t *cand, uint32_t pos, uint32_t sg, uint32_t m) {
-  while (m) {
-    const uint32_t i = __ffs(m) - 1;
-    m &= m - 1;
-    cand[pos++] = (sg << 4) + i;
+// One warp step over super-groups [base, base + kStepSG) of a screened
+// row [s, e) (threshold rt, last super-group glast): the top bytes of 16
+// coins per call; edges with a zero byte join the pending list.
+template <typename Flush>
+__device__ __forceinline__ void step_screened(uint32_t base, uint32_t glast, uint32_t s, uint32_t e, uint32_t rt,
+                                              const CoinKey &ck, uint32_t *pe, uint32_t *pt, uint32_t &npend,
+                                              uint32_t *cand, uint32_t &ncand, uint32_t cap, Flush &&flush) {
+  const uint32_t lane = lane_id();
+  uint32_t z[kSGPL];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < kSGPL; ++q) {
+    const uint32_t g = base + 32 * q + lane;
+    z[q] = g <= glast ? sgroup_zero(g, s, e, ck) : 0u;
+    cnt += __popc(z[q]);
+  }
+  if (__ballot_sync(kFullMask, cnt != 0u) == 0u) return;
+  uint32_t total;
+  const uint32_t excl = warp_excl(cnt, total);
+  if (npend + total > kPend) resolve_pending(pe, pt, npend, cand, ncand, cap, ck, flush);
+  if (total <= kPend) {
+    uint32_t pos = npend + excl;
+#pragma unroll
+    for (uint32_t q = 0; q < kSGPL; ++q) {
+      uint32_t m = z[q];
+      const uint32_t g = base + 32 * q + lane;
+      while (m) {
+        const uint32_t i = __ffs(m) - 1;
+        m &= m - 1;
+        pe[pos] = (g << 4) + i;
+        pt[pos] = rt;
+        ++pos;
+      }
+    }
+    npend += total;
+    __syncwarp();
+    return;
+  }
+  // more zero bytes in one step than the list holds (never seen in practice):
+  // settle them here, one per lane at a time
+  for (;;) {
+    uint32_t x = 0;
+    bool has = false;
+#pragma unroll
+    for (uint32_t q = 0; q < kSGPL; ++q)
+      if (!has && z[q]) {
+        const uint32_t i = __ffs(z[q]) - 1;
+        z[q] &= z[q] - 1;
+        x = ((base + 32 * q + lane) << 4) + i;
+        has = true;
+      }
+    if (__ballot_sync(kFullMask, has) == 0u) break;
+    const bool live = has && resid_live(x, rt, ck);
+    const uint32_t lm = __ballot_sync(kFullMask, live);
+    if (!lm) continue;
+    const uint32_t n = __popc(lm);
+    if (ncand + n > cap) {
+      flush();
+      ncand = 0;
+    }
+    if (live) cand[ncand + __popc(lm & ((1u << lane) - 1u))] = x;
+    ncand += n;
   }
 }
 
@@ -326,7 +399,7 @@ __device__ __forceinline__ void push_live(uint32_t *cand, uint32_t pos, uint32_t
 
 constexpr uint32_t kCandCap = 512;   // per-warp buffer of live edges awaiting their visited test
 static_assert(kCandCap >= 128 * kGPL, "one warp step's live edges fit the buffer");
-static_assert(kCandCap >= 16 * 32, "one super-group per lane's live edges fit the buffer");
+
 
 // Visited set of the common pass: open addressing over kHashSlots 64-bit
 // slots holding epoch << 32 | vertex; a slot whose epoch is not the current
@@ -382,10 +455,12 @@ __device__ __forceinline__ void common_flush(const uint32_t *__restrict__ src, c
 template <bool kOne>
 __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, CommonScratch cs, InstDesc one) {
   __shared__ uint32_t cand_all[8][kCandCap];
+  __shared__ uint32_t pe_all[8][kPend], pt_all[8][kPend];
   const uint32_t lane = lane_id();
   const uint32_t worker = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (worker >= cs.workers) return;
   uint32_t *cand = cand_all[threadIdx.x >> 5];
+  uint32_t *pe = pe_all[threadIdx.x >> 5], *pt = pt_all[threadIdx.x >> 5];
   uint32_t *q = cs.queue + (uint64_t)worker * kQueueCap;
   unsigned long long *ht = cs.hash + (uint64_t)worker * kHashSlots;
   uint32_t epoch = cs.epoch[worker];
@@ -432,7 +507,8 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         rr = rthr[v];
       }
       head += nb;
-      uint32_t ncand = 0;
+      uint32_t ncand = 0, npend = 0;
+      auto flush = [&]() { common_flush(src, cand, ncand, ht, epoch, q, tail, overflow); };
       for (uint32_t b = 0; b < nb && !overflow; ++b) {
         const uint32_t s = __shfl_sync(kFullMask, rs, b), e = __shfl_sync(kFullMask, re, b);
         const uint32_t rt = __shfl_sync(kFullMask, rr, b);
@@ -440,23 +516,8 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         if (screened(rt)) {                    // 16 coins per Philox call
           const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
           scanned += 4 * (g1 - g0 + 1);
-          for (uint32_t base = g0; base <= g1 && !overflow; base += kStepGroups) {
-            uint32_t lv[kGPL];
-            step_live_sg(base, g1, s, e, rt, ck, lv);
-#pragma unroll
-            for (uint32_t qq = 0; qq < kGPL; ++qq) {
-              const uint32_t mine = __popc(lv[qq]);
-              if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
-              uint32_t total;
-              const uint32_t excl = warp_excl(mine, total);   // at most 16 * 32 = kCandCap
-              if (ncand + total > kCandCap) {
-                common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
-                ncand = 0;
-              }
-              push_live_sg(cand, ncand + excl, base + 32 * qq + lane, lv[qq]);
-              ncand += total;
-            }
-          }
+          for (uint32_t base = g0; base <= g1 && !overflow; base += kStepSG)
+            step_screened(base, g1, s, e, rt, ck, pe, pt, npend, cand, ncand, kCandCap, flush);
           continue;
         }
         const uint32_t rl = lim(rt);
@@ -476,6 +537,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
           ncand += total;
         }
       }
+      if (npend) resolve_pending(pe, pt, npend, cand, ncand, kCandCap, ck, flush);
       common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
     }
     if (overflow) {
@@ -493,11 +555,11 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 constexpr uint32_t kRowsPerThread = 2;       // frontier rows each thread loads per block step
 constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step
 constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
+constexpr uint32_t kChunkSG = 512;           // super-groups (8192 in-edges) per chunk of a screened row
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr int kBigBlocksPerSM = 8;          // register cap that keeps 8 blocks (64 warps) per SM
-constexpr uint32_t kBigCand = 512;           // per-warp candidate buffer: one warp step's live edges at most
-static_assert(kBigCand >= 128 * kGPL && kBigCand >= 16 * 32, "a step (or a super-group per lane) fits the buffer");
-static_assert(kChunkGroups % kStepGroups == 0, "a chunk is whole warp steps");
+constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
+static_assert(kChunkGroups % kStepGroups == 0 && kChunkSG % kStepSG == 0, "a chunk is whole warp steps");
 
 // Resolves a warp's buffered live edges: a source not yet in the set joins
 // the queue. Past the queue's capacity the vertex is not kept (its bit is
@@ -536,12 +598,14 @@ __device__ __forceinline__ void block_flush(const uint32_t *__restrict__ src, co
 template <bool kOne>
 __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(SampleLaunch L, BigScratch bs, InstDesc one) {
   __shared__ uint32_t cand_all[kBigWarps][kBigCand];
+  __shared__ uint32_t pe_all[kBigWarps][kPend], pt_all[kBigWarps][kPend];
   __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
   __shared__ uint32_t w_tot[kBigWarps];
   __shared__ unsigned long long s_item, s_base;
   __shared__ uint32_t s_head, s_tail, s_next;
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t *cand = cand_all[warp];
+  uint32_t *pe = pe_all[warp], *pt = pt_all[warp];
   uint32_t *bm = bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot;
   const uint32_t qcap = bs.q_cap;
   uint32_t *q = bs.queue + (uint64_t)blockIdx.x * qcap;
@@ -568,7 +632,8 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       s_tail = 1;
     }
     __syncthreads();
-    uint32_t ncand = 0;                        // this warp's buffered live edges
+    uint32_t ncand = 0, npend = 0;             // this warp's buffered live edges, pending screened edges
+    auto flush = [&]() { block_flush(src, cand, ncand, bm, q, qcap, &s_tail); };
     for (;;) {
       const uint32_t head = s_head, tail = s_tail;
       if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
@@ -584,9 +649,10 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
           b_s[b] = s;
           b_e[b] = e;
           b_rt[b] = rt;
-          // a chunk is kChunkGroups Philox calls: groups of 4 in-edges, or super-groups of 16
-          const uint32_t sh = screened(rt) ? 4u : 2u;
-          nch[r] = (e > s && rt != 0u) ? (((e - 1) >> sh) - (s >> sh) + kChunkGroups) / kChunkGroups : 0u;
+          // a chunk is kChunkGroups groups of 4 in-edges, or kChunkSG super-groups of 16
+          const bool sc = screened(rt);
+          const uint32_t sh = sc ? 4u : 2u, cg = sc ? kChunkSG : kChunkGroups;
+          nch[r] = (e > s && rt != 0u) ? (((e - 1) >> sh) - (s >> sh) + cg) / cg : 0u;
         }
         mine += nch[r];
       }
@@ -627,25 +693,10 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
         const uint32_t s = b_s[lo], e = b_e[lo], rt = b_rt[lo], rl = lim(rt);
         if (screened(rt)) {
           const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
-          const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkGroups;
-          const uint32_t c1 = c0 + kChunkGroups - 1 < g1 ? c0 + kChunkGroups - 1 : g1;
-          for (uint32_t base = c0; base <= c1; base += kStepGroups) {
-            uint32_t lv[kGPL];
-            step_live_sg(base, c1, s, e, rt, ck, lv);
-#pragma unroll
-            for (uint32_t qq = 0; qq < kGPL; ++qq) {
-              const uint32_t mine = __popc(lv[qq]);
-              if (__ballot_sync(kFullMask, mine != 0u) == 0u) continue;
-              uint32_t total;
-              const uint32_t excl = warp_excl(mine, total);
-              if (ncand + total > kBigCand) {
-                block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
-                ncand = 0;
-              }
-              push_live_sg(cand, ncand + excl, base + 32 * qq + lane, lv[qq]);
-              ncand += total;
-            }
-          }
+          const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkSG;
+          const uint32_t c1 = c0 + kChunkSG - 1 < g1 ? c0 + kChunkSG - 1 : g1;
+          for (uint32_t base = c0; base <= c1; base += kStepSG)
+            step_screened(base, c1, s, e, rt, ck, pe, pt, npend, cand, ncand, kBigCand, flush);
           continue;
         }
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
@@ -669,6 +720,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       // at least a batch of queued vertices is still unexpanded, the next
       // batch does not need them, and the warps keep them buffered.
       if (tail - (head + nb) < kBatch) {
+        if (npend) resolve_pending(pe, pt, npend, cand, ncand, kBigCand, ck, flush);
         block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
         ncand = 0;
       }
