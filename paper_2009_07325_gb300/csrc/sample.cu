@@ -30,8 +30,8 @@
 //   more than its edge budget is abandoned and deferred.
 // IC, large-set pass: one 256-thread block per deferred set, with an n-bit
 //   visited bitmap and a queue. Each batch of up to 512 frontier
-//   vertices is cut into chunks of at most 512 Philox calls (2048 in-edges,
-//   or 8192 in a super-group row) that the block's
+//   vertices is cut into chunks of at most 2048 in-edges (512 Philox calls),
+//   or 4096 in a super-group row (256 calls), that the block's
 //   warps take from a shared counter, so the heavy tail of huge RR sets is
 //   spread over 8 warps. Only __syncthreads barriers are used.
 // LT: the reverse walk of Sec. III-G (four walks per warp in the common pass, see
@@ -267,7 +267,7 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t mine, uint32_t &total) {
 constexpr uint32_t kGPL = 2;
 constexpr uint32_t kStepGroups = 32 * kGPL;
 // Super-groups (of 16 in-edges) each lane scans per warp step in a screened row.
-constexpr uint32_t kSGPL = 2;
+constexpr uint32_t kSGPL = 4;
 constexpr uint32_t kStepSG = 32 * kSGPL;
 
 // Coins of one warp step over groups [base, base + kStepGroups) of the row
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 constexpr uint32_t kRowsPerThread = 2;       // frontier rows each thread loads per block step
 constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step
 constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
-constexpr uint32_t kChunkSG = 512;           // super-groups (8192 in-edges) per chunk of a screened row
+constexpr uint32_t kChunkSG = 256;           // super-groups (4096 in-edges) per chunk of a screened row
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr int kBigBlocksPerSM = 8;          // register cap that keeps 8 blocks (64 warps) per SM
 constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
