@@ -74,9 +74,12 @@ void gim_destroy(gim_ctx *ctx);
  *   in_offsets: n+1 entries, in_offsets[0] = 0, non-decreasing, last = m.
  *   in_sources: m entries, each < n, strictly ascending within a row.
  *   in_weights: m entries.
- * Precomputes the IC coin thresholds and the LT cumulative thresholds
- * (Sec. III-G). The graph is usable under LT only if every row's weights
- * sum to at most 1 + 1e-6 (Sec. II-B); gim_graph_lt_valid reports it.
+ * Precomputes the IC coin thresholds; the LT cumulative thresholds
+ * (Sec. III-G) are built on the first LT use (gim_graph_lt_valid, an LT
+ * call, gim_server_start), so IC work never waits for them. The graph is
+ * usable under LT only if every row's weights sum to at most 1 + 1e-6
+ * (Sec. II-B); gim_graph_lt_valid reports it. The weights stay on the
+ * device (4m bytes) for that purpose.
  * Replaces any previous graph and empties the RR collection.
  * Limits: 2 <= n < 2^32 - 1, m < 2^32 - 4.
  * Errors: GIM_ERR_ARG (violated layout or range; the context is unchanged),
@@ -85,7 +88,8 @@ void gim_destroy(gim_ctx *ctx);
 gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *in_offsets,
                           const uint32_t *in_sources, const float *in_weights);
 
-/* *out = 1 if the loaded graph satisfies the LT weight condition, else 0. */
+/* *out = 1 if the loaded graph satisfies the LT weight condition, else 0
+   (builds the LT thresholds if no LT call has yet). */
 gim_status gim_graph_lt_valid(gim_ctx *ctx, int *out);
 
 /*

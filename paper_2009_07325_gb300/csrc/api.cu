@@ -34,6 +34,7 @@ void free_graph(DevGraph &g) {
   dfree(g.rthr);
   dfree(g.rw);
   dfree(g.cum);
+  dfree(g.w);
   g = DevGraph{};
 }
 
@@ -133,7 +134,7 @@ gim_status run_imm(gim_ctx *ctx, gim_model model, uint32_t T, uint32_t k, double
   if (k == 0 || k > ctx->g.n || !seeds_out) return set_err(ctx, GIM_ERR_ARG, "need 1 <= k <= n and seeds_out");
   if (!(eps > 0.0 && eps < 1.0)) return set_err(ctx, GIM_ERR_ARG, "eps must be in (0, 1)");
   if (!(ell > 0.0)) return set_err(ctx, GIM_ERR_ARG, "ell must be > 0");
-  if (model == GIM_LT && !ctx->lt_ok) return set_err(ctx, GIM_ERR_ARG, "graph weights are not valid for LT");
+  if (model == GIM_LT && !lt_valid(ctx)) return set_err(ctx, GIM_ERR_ARG, "graph weights are not valid for LT");
   if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
   if (T > 1 && (st = gim_rr_set_rounds(ctx, T)) != GIM_OK) return st;
 
@@ -277,13 +278,11 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   DevGraph g;
   g.n = n;
   g.m = m;
-  float *d_w = nullptr;
   unsigned int *d_flags = nullptr;
   unsigned int flags = 0;
   cudaError_t e = cudaSuccess;
   auto bail = [&](cudaError_t err, const char *what) {
     free_graph(g);
-    dfree(d_w);
     dfree(d_flags);
     return cuda_err(ctx, err, what);
   };
@@ -292,8 +291,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   if ((e = cudaMalloc(&g.thr, m_pad * 4)) != cudaSuccess) return bail(e, "alloc thresholds");
   if ((e = cudaMalloc(&g.rthr, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row thresholds");
   if ((e = cudaMalloc(&g.rw, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row weights");
-  if ((e = cudaMalloc(&g.cum, std::max<uint64_t>(m, 1) * 8)) != cudaSuccess) return bail(e, "alloc lt thresholds");
-  if ((e = cudaMalloc(&d_w, std::max<uint64_t>(m, 1) * 4)) != cudaSuccess) return bail(e, "alloc weights");
+  if ((e = cudaMalloc(&g.w, std::max<uint64_t>(m, 1) * 4)) != cudaSuccess) return bail(e, "alloc weights");
   if ((e = cudaMalloc(&d_flags, 4)) != cudaSuccess) return bail(e, "alloc flags");
   cudaStream_t s = ctx->stream;
   if ((e = cudaMemcpyAsync(g.off, off32.data(), ((uint64_t)n + 1) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -302,15 +300,14 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   if (m) {
     if ((e = cudaMemcpyAsync(g.src, in_sources, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return bail(e, "upload sources");
-    if ((e = cudaMemcpyAsync(d_w, in_weights, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(g.w, in_weights, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return bail(e, "upload weights");
   }
   if ((e = cudaMemsetAsync(d_flags, 0, 4, s)) != cudaSuccess) return bail(e, "clear flags");
-  if ((e = launch_graph_prep(g, d_w, d_flags, s)) != cudaSuccess) return bail(e, "graph preprocessing");
+  if ((e = launch_graph_prep(g, d_flags, s)) != cudaSuccess) return bail(e, "graph preprocessing");
   ctx->launches += 2;
   if ((e = cudaMemcpyAsync(&flags, d_flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return bail(e, "flags");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "graph preprocessing");
-  dfree(d_w);
   dfree(d_flags);
   if (flags & (kGraphBadSource | kGraphNotAscending | kGraphBadWeight)) {
     free_graph(g);
@@ -325,7 +322,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   ctx->owns_graph = true;
   ctx->g = g;
   ctx->has_graph = true;
-  ctx->lt_ok = (flags & kGraphNotLT) ? 0 : 1;
+  ctx->lt_ok = -1;   // the LT thresholds are built on the first LT use
   ctx->max_indeg = max_indeg;
   dfree(ctx->st.cnt);
   free_select(ctx->sel);
@@ -346,6 +343,7 @@ gim_status gim_graph_lt_valid(gim_ctx *ctx, int *out) {
   if (st) return st;
   if (!out) return set_err(ctx, GIM_ERR_ARG, "out is null");
   if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
+  if ((st = ensure_lt(ctx)) != GIM_OK) return st;
   *out = ctx->lt_ok;
   return GIM_OK;
 }
@@ -356,7 +354,7 @@ gim_status gim_sample_rr(gim_ctx *ctx, gim_model model, uint64_t count, uint64_t
   const auto t0 = std::chrono::steady_clock::now();
   if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
   if (model != GIM_IC && model != GIM_LT) return set_err(ctx, GIM_ERR_ARG, "unknown model");
-  if (model == GIM_LT && !ctx->lt_ok) return set_err(ctx, GIM_ERR_ARG, "graph weights are not valid for LT");
+  if (model == GIM_LT && !lt_valid(ctx)) return set_err(ctx, GIM_ERR_ARG, "graph weights are not valid for LT");
   if (ctx->R > 0 && (ctx->model != (int)model || ctx->seed != seed))
     return set_err(ctx, GIM_ERR_STATE, "model/seed differ from the stored collection; call gim_reset_rr");
   if (ctx->R + count >= 0xFFFFFFFFull) return set_err(ctx, GIM_ERR_ARG, "more than 2^32-2 RR sets");
@@ -471,7 +469,7 @@ gim_status gim_batch_imm(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_pa
     if (p.k == 0 || p.k > c->g.n || !seeds_out[i]) return set_err(ctx, GIM_ERR_ARG, "instance %u: bad k or seeds", i);
     if (!(p.eps > 0.0 && p.eps < 1.0)) return set_err(ctx, GIM_ERR_ARG, "instance %u: eps not in (0, 1)", i);
     if (!(p.ell > 0.0)) return set_err(ctx, GIM_ERR_ARG, "instance %u: ell <= 0", i);
-    if (p.model == GIM_LT && !c->lt_ok) return set_err(ctx, GIM_ERR_ARG, "instance %u: graph not LT-valid", i);
+    if (p.model == GIM_LT && !lt_valid(c)) return set_err(ctx, GIM_ERR_ARG, "instance %u: graph not LT-valid", i);
   }
   return batch_imm(ctxs, n_inst, params, seeds_out, results);
 }
@@ -519,7 +517,7 @@ gim_status gim_autotune(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_par
   for (uint32_t i = 0; i < n_inst; ++i) {
     if (!ctxs[i] || ctxs[i]->device != ctx->device) return set_err(ctx, GIM_ERR_ARG, "instance %u: bad context", i);
     if (!ctxs[i]->has_graph) return set_err(ctx, GIM_ERR_STATE, "instance %u: no graph loaded", i);
-    if (params[i].model == GIM_LT && !ctxs[i]->lt_ok) return set_err(ctx, GIM_ERR_ARG, "instance %u: not LT-valid", i);
+    if (params[i].model == GIM_LT && !lt_valid(ctxs[i])) return set_err(ctx, GIM_ERR_ARG, "instance %u: not LT-valid", i);
   }
   return autotune(ctxs, n_inst, params, sample_sets == 0 ? 2000 : sample_sets, budget_out, measured_out);
 }

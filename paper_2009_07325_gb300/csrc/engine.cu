@@ -105,6 +105,31 @@ ImmConst imm_constants(uint32_t n, uint32_t k, double eps, double ell) { return 
 
 DeviceShared &device_shared(int device) { return g_shared[device]; }
 
+gim_status ensure_lt(gim_ctx *ctx) {
+  if (!ctx->has_graph) return set_err(ctx, GIM_ERR_STATE, "no graph loaded");
+  if (ctx->lt_ok >= 0) return GIM_OK;
+  if (!ctx->owns_graph) return set_err(ctx, GIM_ERR_STATE, "the LT thresholds of a shared graph are not built");
+  DevGraph &g = ctx->g;
+  cudaStream_t s = ctx->stream;
+  if (!g.cum) CU(cudaMalloc(&g.cum, std::max<uint64_t>(g.m, 1) * 8));
+  unsigned int *d_flags = nullptr;
+  CU(cudaMalloc(&d_flags, 4));
+  unsigned int flags = 0;
+  cudaError_t e = cudaMemsetAsync(d_flags, 0, 4, s);
+  if (e == cudaSuccess) e = launch_lt_prep(g, d_flags, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_flags, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_flags);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "LT thresholds");
+  ctx->launches++;
+  ctx->lt_ok = (flags & kGraphNotLT) ? 0 : 1;
+  return GIM_OK;
+}
+
+// True iff the graph is LT-valid, building its LT thresholds first if needed
+// (a failure to build them leaves the error on ctx and reads as not valid).
+bool lt_valid(gim_ctx *ctx) { return ensure_lt(ctx) == GIM_OK && ctx->lt_ok == 1; }
+
 gim_status shared_acquire(gim_ctx *ctx) {
   DeviceShared &D = g_shared[ctx->device];
   std::lock_guard<std::mutex> lock(D.mu);

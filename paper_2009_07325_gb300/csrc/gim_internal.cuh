@@ -115,7 +115,8 @@ struct DevGraph {
   uint32_t *src = nullptr;   // m rounded up to a multiple of 4, zero padded
   uint32_t *thr = nullptr;   // same length: IC coin threshold ceil(w * 2^24)
   uint32_t *rthr = nullptr;  // n: the row's common threshold when all its in-edges share one, else kPerEdge
-  uint64_t *cum = nullptr;   // m: LT cumulative thresholds in 2^-32 units
+  uint64_t *cum = nullptr;   // m: LT cumulative thresholds in 2^-32 units (built on the first LT use)
+  float *w = nullptr;        // m: the fp32 weights as loaded (the LT thresholds are built from them)
   uint32_t *rw = nullptr;    // n: fp32 bits of the row's common weight when all its in-edges share one, else kPerEdge
 };
 
@@ -226,7 +227,9 @@ int ic_common_blocks_per_sm();
 int lt_common_blocks_per_sm();
 
 // Graph preprocessing (graph.cu).
-cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_flags, cudaStream_t s);
+cudaError_t launch_graph_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s);
+// The LT thresholds g.cum (allocated by the caller) from g.w; kGraphNotLT in *d_flags if a row sums above 1.
+cudaError_t launch_lt_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s);
 enum : unsigned int { kGraphBadSource = 1u, kGraphNotAscending = 2u, kGraphBadWeight = 4u, kGraphNotLT = 8u };
 
 // Selection buffers of one instance (grown on demand, kept between calls).
@@ -334,6 +337,10 @@ struct SampleJobH {
 gim_status mrim_sample(gim_ctx *ctx, int model, uint64_t seed, uint64_t count);
 // Frees ctx's per-round views and the merge scratch.
 void mrim_release(gim_ctx *ctx);
+// Builds the LT thresholds of ctx's graph on its first LT use and sets
+// ctx->lt_ok (a graph shared from another context must have them already).
+gim_status ensure_lt(gim_ctx *ctx);
+bool lt_valid(gim_ctx *ctx);
 
 // IMM constants (Tang, Shi, Xiao 2015): ell', eps', lambda', lambda*, and
 // the number of lower-bound rounds floor(log2 n) - 1.
@@ -433,7 +440,7 @@ struct gim_ctx {
 
   bool has_graph = false;
   bool owns_graph = true;         // false for a server pool that shares another context's graph
-  int lt_ok = 0;
+  int lt_ok = -1;                 // 1 / 0: LT-valid or not; -1: not known yet (LT thresholds not built)
   uint32_t max_indeg = 0;         // of the loaded graph (degree profile of the autotuner)
   gim::DevGraph g;
 

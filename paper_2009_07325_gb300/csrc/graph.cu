@@ -1,6 +1,6 @@
-// Graph preprocessing on the device: validation of the in-edge CSR, the IC
-// coin thresholds and the LT cumulative thresholds (Sec. III-B CSR layout;
-// Sec. III-G LT edge choice).
+// Graph preprocessing on the device: validation of the in-edge CSR and the IC
+// coin thresholds at load, the LT cumulative thresholds on the first LT use
+// (Sec. III-B CSR layout; Sec. III-G LT edge choice).
 #include <algorithm>
 
 #include "gim_internal.cuh"
@@ -59,10 +59,45 @@ __device__ __forceinline__ unsigned long long lt_round(double P) {
   return c > 4294967296ull ? 4294967296ull : c;
 }
 
-// Warp per row: ascending sources within the row, the row's common IC
-// threshold (rthr), the row's common weight (rw: the fp32 bits when every
-// in-edge of the row carries the same weight, else kPerEdge), and the LT
-// thresholds
+// Warp per row, at graph load: ascending sources within the row, the row's
+// common IC threshold (rthr) and the row's common weight (rw: the fp32 bits
+// when every in-edge of the row carries the same weight, else kPerEdge).
+__global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off,
+                                                        const uint32_t *__restrict__ src,
+                                                        const float *__restrict__ w,
+                                                        const uint32_t *__restrict__ thr,
+                                                        uint32_t *__restrict__ rthr, uint32_t *__restrict__ rw,
+                                                        unsigned int *__restrict__ flags) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned int bad = 0;
+  for (uint32_t v = warp; v < n; v += nwarps) {
+    const uint32_t s = off[v], e = off[v + 1];
+    const uint32_t common0 = e > s ? thr[s] : 0u;
+    const uint32_t w0 = e > s ? __float_as_uint(w[s]) : kPerEdge;
+    bool differs = false, wdiffers = false;
+    for (uint32_t base = s; base < e; base += 32) {
+      const uint32_t i = base + lane;
+      const bool in = i < e;
+      const uint32_t si = in ? src[i] : 0u;
+      if (in && thr[i] != common0) differs = true;
+      if (in && __float_as_uint(w[i]) != w0) wdiffers = true;
+      uint32_t prev = __shfl_up_sync(kFullMask, si, 1);
+      if (lane == 0 && base > s) prev = src[base - 1];
+      if (in && i > s && !(prev < si)) bad |= kGraphNotAscending;
+    }
+    const bool any_diff = __any_sync(kFullMask, differs);
+    const bool any_wdiff = __any_sync(kFullMask, wdiffers);
+    if (lane == 0) {
+      rthr[v] = any_diff ? kPerEdge : common0;
+      rw[v] = any_wdiff ? kPerEdge : w0;
+    }
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+// Warp per row, on the first LT use of the graph: the LT thresholds
 //   cum[e_i] = min(2^32, round_half_up(P_i * 2^32)),
 // P_i the fp64 running sum of the row's weights in CSR order; a row summing
 // to within 1e-6 of 1 gets cum[last] = 2^32 so that it always selects an
@@ -74,39 +109,23 @@ __device__ __forceinline__ unsigned long long lt_round(double P) {
 // the integer prefix sum times 2^E, which the warp computes with a parallel
 // scan. Other rows (weights spanning more than 2^39, or huge sums) take the
 // strictly sequential fp64 loop. Both give the same P_i.
-__global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off,
-                                                        const uint32_t *__restrict__ src,
-                                                        const float *__restrict__ w,
-                                                        const uint32_t *__restrict__ thr,
-                                                        uint32_t *__restrict__ rthr, uint64_t *__restrict__ cum,
-                                                        uint32_t *__restrict__ rw, unsigned int *__restrict__ flags) {
+__global__ void __launch_bounds__(256) prep_lt_kernel(uint32_t n, const uint32_t *__restrict__ off,
+                                                      const float *__restrict__ w, uint64_t *__restrict__ cum,
+                                                      unsigned int *__restrict__ flags) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned int bad = 0;
   for (uint32_t v = warp; v < n; v += nwarps) {
     const uint32_t s = off[v], e = off[v + 1];
-    const uint32_t common0 = e > s ? thr[s] : 0u;
-    const uint32_t w0 = e > s ? __float_as_uint(w[s]) : kPerEdge;
-    bool differs = false, wdiffers = false;
     int emin = 0x7FFFFFFF;
-    // pass 1: checks, smallest ulp exponent
-    for (uint32_t base = s; base < e; base += 32) {
-      const uint32_t i = base + lane;
-      const bool in = i < e;
-      const uint32_t si = in ? src[i] : 0u;
-      if (in && thr[i] != common0) differs = true;
-      if (in && __float_as_uint(w[i]) != w0) wdiffers = true;
-      uint32_t prev = __shfl_up_sync(kFullMask, si, 1);
-      if (lane == 0 && base > s) prev = src[base - 1];
-      if (in && i > s && !(prev < si)) bad |= kGraphNotAscending;
+    for (uint32_t i = s + lane; i < e; i += 32) {   // smallest ulp exponent
       uint32_t mant;
-      const int ex = in ? ulp_exponent(w[i], &mant) : 0x7FFFFFFF;
-      emin = min(emin, ex);
+      emin = min(emin, ulp_exponent(w[i], &mant));
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) emin = min(emin, __shfl_xor_sync(kFullMask, emin, d));
-    // pass 2: exact parallel prefix sums when no fp64 addition can round
+    // exact parallel prefix sums when no fp64 addition can round
     bool exact = true;
     unsigned long long carry = 0;
     double scale = 1.0;
@@ -157,11 +176,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
         if (i < e) cum[i] = lt_round(mine);
       }
     }
-    const bool any_diff = __any_sync(kFullMask, differs);
-    const bool any_wdiff = __any_sync(kFullMask, wdiffers);
     if (lane == 0) {
-      rthr[v] = any_diff ? kPerEdge : common0;
-      rw[v] = any_wdiff ? kPerEdge : w0;
       if (e > s && fabs(__dsub_rn(P, 1.0)) <= 1e-6) cum[e - 1] = 4294967296ull;
       if (P > 1.0 + 1e-6) bad |= kGraphNotLT;
     }
@@ -169,16 +184,23 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
   if (bad) atomicOr(flags, bad);
 }
 
-cudaError_t launch_graph_prep(DevGraph &g, const float *d_w, unsigned int *d_flags, cudaStream_t s) {
+cudaError_t launch_graph_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s) {
   const uint64_t m_pad = (g.m + 3) / 4 * 4 + 4;
   int blocks = (int)std::min<uint64_t>((m_pad + 255) / 256, 152ull * 16);
   if (blocks < 1) blocks = 1;
-  prep_edges_kernel<<<blocks, 256, 0, s>>>(g.n, g.m, m_pad, g.src, d_w, g.thr, d_flags);
+  prep_edges_kernel<<<blocks, 256, 0, s>>>(g.n, g.m, m_pad, g.src, g.w, g.thr, d_flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 7) / 8, 152ull * 16);
   if (rb < 1) rb = 1;
-  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, d_w, g.thr, g.rthr, g.cum, g.rw, d_flags);
+  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, g.w, g.thr, g.rthr, g.rw, d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lt_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s) {
+  int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 7) / 8, 152ull * 16);
+  if (rb < 1) rb = 1;
+  prep_lt_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.w, g.cum, d_flags);
   return cudaGetLastError();
 }
 

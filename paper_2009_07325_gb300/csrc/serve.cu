@@ -349,6 +349,10 @@ gim_status gim_server_start(gim_server **out, gim_ctx *graph_ctx, uint32_t max_a
   if (max_active == 0 || max_active > 1024 || max_k == 0 || max_k > graph_ctx->g.n)
     return set_err(graph_ctx, GIM_ERR_ARG, "need 1 <= max_active <= 1024 and 1 <= max_k <= n");
   if (cudaSetDevice(graph_ctx->device) != cudaSuccess) return cuda_err(graph_ctx, cudaGetLastError(), "device");
+  {   // LT queries are served from the shared graph's thresholds: build them now
+    const gim_status lt = ensure_lt(graph_ctx);
+    if (lt != GIM_OK) return lt;
+  }
   auto S = std::make_unique<gim_server>();
   S->graph = graph_ctx;
   S->max_active = max_active;
