@@ -615,6 +615,8 @@ def run_ours(args):
     off_p, src_p, w_p = pin(g.offsets), pin(g.sources), pin(g.weights)
     h2d = off_p.nbytes + src_p.nbytes + w_p.nbytes
     e2e_t, e2e_units = 0.0, 0
+    ctx.graph_load(g.n, off_p, src_p, w_p)    # untimed warm-up: the first load allocates the graph arrays
+    run_once()
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -35,6 +35,7 @@ void free_graph(DevGraph &g) {
   dfree(g.rw);
   dfree(g.cum);
   dfree(g.w);
+  dfree(g.off64);
   g = DevGraph{};
 }
 
@@ -241,6 +242,7 @@ void gim_destroy(gim_ctx *ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   mrim_release(ctx);
   if (ctx->owns_graph) free_graph(ctx->g);
+  free_graph(ctx->g_spare);
   dfree(ctx->st.members);
   dfree(ctx->st.rr_start);
   dfree(ctx->st.rr_len);
@@ -266,73 +268,99 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   if (m >= 0xFFFFFFFCull) return set_err(ctx, GIM_ERR_ARG, "m must be below 2^32-4");
   if (!in_offsets || (m > 0 && (!in_sources || !in_weights))) return set_err(ctx, GIM_ERR_ARG, "null input array");
   if (in_offsets[0] != 0 || in_offsets[n] != m) return set_err(ctx, GIM_ERR_ARG, "offsets must start at 0 and end at m");
-  std::vector<uint32_t> off32((size_t)n + 1);
-  uint32_t max_indeg = 0;
-  for (uint64_t v = 0; v <= n; ++v) {
-    if (v > 0 && in_offsets[v] < in_offsets[v - 1]) return set_err(ctx, GIM_ERR_ARG, "offsets decrease at row %llu",
-                                                                   (unsigned long long)v - 1);
-    off32[v] = (uint32_t)in_offsets[v];
-    if (v > 0) max_indeg = std::max<uint32_t>(max_indeg, off32[v] - off32[v - 1]);
-  }
   const uint64_t m_pad = (m + 3) / 4 * 4 + 4;
+  cudaStream_t s = ctx->stream;
+  // the arrays: those of the graph before the current one when they are large enough
   DevGraph g;
-  g.n = n;
-  g.m = m;
-  unsigned int *d_flags = nullptr;
-  unsigned int flags = 0;
+  if (ctx->g_spare.off && ctx->g_spare.n_cap >= n && ctx->g_spare.m_cap >= m_pad) {
+    g = ctx->g_spare;
+    ctx->g_spare = DevGraph{};
+  } else {
+    free_graph(ctx->g_spare);
+  }
+  unsigned int *d_info = nullptr;   // flags, first decreasing row, largest in-degree, big-row count
+  unsigned int info[4] = {0, 0, 0, 0};
   cudaError_t e = cudaSuccess;
   auto bail = [&](cudaError_t err, const char *what) {
     free_graph(g);
-    dfree(d_flags);
+    dfree(d_info);
     return cuda_err(ctx, err, what);
   };
-  if ((e = cudaMalloc(&g.off, ((uint64_t)n + 1) * 4)) != cudaSuccess) return bail(e, "alloc offsets");
-  if ((e = cudaMalloc(&g.src, m_pad * 4)) != cudaSuccess) return bail(e, "alloc sources");
-  if ((e = cudaMalloc(&g.thr, m_pad * 4)) != cudaSuccess) return bail(e, "alloc thresholds");
-  if ((e = cudaMalloc(&g.rthr, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row thresholds");
-  if ((e = cudaMalloc(&g.rw, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row weights");
-  if ((e = cudaMalloc(&g.w, std::max<uint64_t>(m, 1) * 4)) != cudaSuccess) return bail(e, "alloc weights");
-  if ((e = cudaMalloc(&d_flags, 4)) != cudaSuccess) return bail(e, "alloc flags");
-  cudaStream_t s = ctx->stream;
-  if ((e = cudaMemcpyAsync(g.off, off32.data(), ((uint64_t)n + 1) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if (!g.off) {
+    g.n_cap = n;
+    g.m_cap = m_pad;
+    if ((e = cudaMalloc(&g.off, ((uint64_t)n + 1) * 4)) != cudaSuccess) return bail(e, "alloc offsets");
+    if ((e = cudaMalloc(&g.off64, ((uint64_t)n + 1) * 8)) != cudaSuccess) return bail(e, "alloc offsets");
+    if ((e = cudaMalloc(&g.src, m_pad * 4)) != cudaSuccess) return bail(e, "alloc sources");
+    if ((e = cudaMalloc(&g.thr, m_pad * 4)) != cudaSuccess) return bail(e, "alloc thresholds");
+    if ((e = cudaMalloc(&g.rthr, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row thresholds");
+    if ((e = cudaMalloc(&g.rw, (uint64_t)n * 4)) != cudaSuccess) return bail(e, "alloc row weights");
+    if ((e = cudaMalloc(&g.w, m_pad * 4)) != cudaSuccess) return bail(e, "alloc weights");
+  }
+  g.n = n;
+  g.m = m;
+  if ((e = cudaMalloc(&d_info, 4 * sizeof(unsigned int))) != cudaSuccess) return bail(e, "alloc flags");
+  // a graph that fails validation leaves its arrays for the next load and the context as it was
+  auto reject = [&]() {
+    ctx->g_spare = g;
+    dfree(d_info);
+  };
+  if ((e = cudaMemcpyAsync(g.off64, in_offsets, ((uint64_t)n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return bail(e, "upload offsets");
-  if ((e = cudaMemsetAsync(g.src, 0, m_pad * 4, s)) != cudaSuccess) return bail(e, "clear sources");
+  if ((e = cudaMemsetAsync(g.src + m, 0, (m_pad - m) * 4, s)) != cudaSuccess) return bail(e, "clear padding");
   if (m) {
     if ((e = cudaMemcpyAsync(g.src, in_sources, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return bail(e, "upload sources");
     if ((e = cudaMemcpyAsync(g.w, in_weights, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return bail(e, "upload weights");
   }
-  if ((e = cudaMemsetAsync(d_flags, 0, 4, s)) != cudaSuccess) return bail(e, "clear flags");
-  if ((e = launch_graph_prep(g, d_flags, s)) != cudaSuccess) return bail(e, "graph preprocessing");
-  ctx->launches += 2;
-  if ((e = cudaMemcpyAsync(&flags, d_flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return bail(e, "flags");
+  if ((e = cudaMemsetAsync(d_info, 0, 4, s)) != cudaSuccess) return bail(e, "clear flags");
+  if ((e = cudaMemsetAsync(d_info + 1, 0xFF, 4, s)) != cudaSuccess) return bail(e, "clear flags");
+  if ((e = cudaMemsetAsync(d_info + 2, 0, 8, s)) != cudaSuccess) return bail(e, "clear flags");
+  if ((e = launch_offsets_prep(g, d_info, s)) != cudaSuccess) return bail(e, "offsets");
+  if ((e = cudaMemcpyAsync(info, d_info, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return bail(e, "offsets");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "offsets");
+  ctx->launches += 1;
+  if (info[0] & kGraphBadOffsets) {
+    reject();
+    return set_err(ctx, GIM_ERR_ARG, "offsets decrease at row %u", info[1]);
+  }
+  const uint32_t max_indeg = info[2];
+  // offsets are valid (non-decreasing from 0 to m): the edge and row passes stay in bounds
+  if ((e = launch_graph_prep(g, d_info, s)) != cudaSuccess) return bail(e, "graph preprocessing");
+  ctx->launches += 3;
+  if ((e = cudaMemcpyAsync(info, d_info, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return bail(e, "flags");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "graph preprocessing");
-  dfree(d_flags);
+  const unsigned int flags = info[0];
   if (flags & (kGraphBadSource | kGraphNotAscending | kGraphBadWeight)) {
-    free_graph(g);
+    reject();
     return set_err(ctx, GIM_ERR_ARG, "%s%s%s", (flags & kGraphBadSource) ? "source id >= n; " : "",
                    (flags & kGraphNotAscending) ? "sources not strictly ascending within a row; " : "",
                    (flags & kGraphBadWeight) ? "weight outside [0, 1]; " : "");
   }
+  dfree(d_info);
 
-  // commit: replace the graph and empty the collection
-  cudaStreamSynchronize(s);
-  if (ctx->owns_graph) free_graph(ctx->g);
+  // commit: replace the graph (its arrays are kept for the next load) and empty the collection
+  if (ctx->owns_graph && ctx->g.off) {
+    free_graph(ctx->g_spare);
+    ctx->g_spare = ctx->g;
+  }
   ctx->owns_graph = true;
   ctx->g = g;
   ctx->has_graph = true;
   ctx->lt_ok = -1;   // the LT thresholds are built on the first LT use
   ctx->max_indeg = max_indeg;
-  dfree(ctx->st.cnt);
-  free_select(ctx->sel);
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
   ctx->jhi = ctx->rhi = 0;
   ctx->rounds = 1;
-  ctx->cnt_cap = 0;
-  CU(cudaMalloc(&ctx->st.cnt, (uint64_t)n * 4 + 16));
-  ctx->cnt_cap = (uint64_t)n + 4;
+  if (ctx->cnt_cap < (uint64_t)n + 4) {
+    dfree(ctx->st.cnt);
+    ctx->cnt_cap = 0;
+    CU(cudaMalloc(&ctx->st.cnt, (uint64_t)n * 4 + 16));
+    ctx->cnt_cap = (uint64_t)n + 4;
+  }
   CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)n * 4 + 16, s));
   CU(cudaStreamSynchronize(s));
   return GIM_OK;

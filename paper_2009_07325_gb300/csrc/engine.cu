@@ -111,7 +111,7 @@ gim_status ensure_lt(gim_ctx *ctx) {
   if (!ctx->owns_graph) return set_err(ctx, GIM_ERR_STATE, "the LT thresholds of a shared graph are not built");
   DevGraph &g = ctx->g;
   cudaStream_t s = ctx->stream;
-  if (!g.cum) CU(cudaMalloc(&g.cum, std::max<uint64_t>(g.m, 1) * 8));
+  if (!g.cum) CU(cudaMalloc(&g.cum, std::max<uint64_t>(g.m_cap, 1) * 8));
   unsigned int *d_flags = nullptr;
   CU(cudaMalloc(&d_flags, 4));
   unsigned int flags = 0;
@@ -189,7 +189,7 @@ gim_status ensure_big(gim_ctx *ctx, DeviceShared &D, uint32_t n, bool full_queue
   const uint64_t words = ((uint64_t)n + 31) / 32;
   const uint64_t wps = (words + 31) / 32 * 32;
   const uint64_t per = wps * 4 + (uint64_t)qc * 4;
-  uint64_t slots = std::min<uint64_t>(budget / std::max<uint64_t>(per, 1), (uint64_t)D.sm_count * 8);
+  uint64_t slots = std::min<uint64_t>(budget / std::max<uint64_t>(per, 1), (uint64_t)D.sm_count * kBigBlocksPerSM);
   slots = std::max<uint64_t>(slots, 1);
   CU(cudaMalloc(&D.big.bitmap, wps * 4 * slots));
   CU(cudaMalloc(&D.big.queue, (uint64_t)qc * 4 * slots));

@@ -118,6 +118,9 @@ struct DevGraph {
   uint64_t *cum = nullptr;   // m: LT cumulative thresholds in 2^-32 units (built on the first LT use)
   float *w = nullptr;        // m: the fp32 weights as loaded (the LT thresholds are built from them)
   uint32_t *rw = nullptr;    // n: fp32 bits of the row's common weight when all its in-edges share one, else kPerEdge
+  uint64_t *off64 = nullptr; // n+1: the offsets as uploaded (validated and narrowed on the device)
+  uint32_t n_cap = 0;        // the arrays hold graphs of up to n_cap vertices and m_cap (padded) edges
+  uint64_t m_cap = 0;
 };
 
 constexpr uint32_t kPerEdge = 0xFFFFFFFFu;   // rthr value of a row whose thresholds differ
@@ -212,6 +215,7 @@ struct BigScratch {
 constexpr uint32_t kSlotQueue = 1u << 20;   // queue entries per slot in the first large-set pass
 
 constexpr int kBigBlock = 256;
+constexpr int kBigBlocksPerSM = 8;   // block-per-set pass: blocks (slots) per SM, 32 registers per thread
 
 // Host launchers (sample.cu).
 // `one` (nullable): the launch's only instance, passed by value so that the
@@ -227,10 +231,18 @@ int ic_common_blocks_per_sm();
 int lt_common_blocks_per_sm();
 
 // Graph preprocessing (graph.cu).
+// Offsets: info[0] |= kGraphBadOffsets and info[1] = the first row whose
+// offsets decrease (info[1] must start at ~0u), info[2] = the largest
+// in-degree; g.off gets the offsets narrowed to 32 bits.
+cudaError_t launch_offsets_prep(DevGraph &g, unsigned int *info, cudaStream_t s);
+// IC thresholds and row checks; d_flags[0] collects kGraph* flags and
+// d_flags[3] (zero on entry) counts the rows listed for the warp pass.
 cudaError_t launch_graph_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s);
 // The LT thresholds g.cum (allocated by the caller) from g.w; kGraphNotLT in *d_flags if a row sums above 1.
 cudaError_t launch_lt_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s);
-enum : unsigned int { kGraphBadSource = 1u, kGraphNotAscending = 2u, kGraphBadWeight = 4u, kGraphNotLT = 8u };
+enum : unsigned int {
+  kGraphBadSource = 1u, kGraphNotAscending = 2u, kGraphBadWeight = 4u, kGraphNotLT = 8u, kGraphBadOffsets = 16u
+};
 
 // Selection buffers of one instance (grown on demand, kept between calls).
 // Vertices that lie in many RR sets ("hubs": count >= a threshold chosen per
@@ -443,6 +455,7 @@ struct gim_ctx {
   int lt_ok = -1;                 // 1 / 0: LT-valid or not; -1: not known yet (LT thresholds not built)
   uint32_t max_indeg = 0;         // of the loaded graph (degree profile of the autotuner)
   gim::DevGraph g;
+  gim::DevGraph g_spare;          // the arrays of the previous graph, reused by the next load that fits
 
   // RR collection
   int model = -1;

@@ -59,20 +59,59 @@ __device__ __forceinline__ unsigned long long lt_round(double P) {
   return c > 4294967296ull ? 4294967296ull : c;
 }
 
-// Warp per row, at graph load: ascending sources within the row, the row's
+// At graph load, per row: ascending sources within the row, the row's
 // common IC threshold (rthr) and the row's common weight (rw: the fp32 bits
 // when every in-edge of the row carries the same weight, else kPerEdge).
+// Rows of at most kSmallRow in-edges take one thread each; the others are
+// listed (big, count in *nbig) for a warp each (prep_big_rows_kernel).
+constexpr uint32_t kSmallRow = 64;
+
 __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off,
                                                         const uint32_t *__restrict__ src,
                                                         const float *__restrict__ w,
                                                         const uint32_t *__restrict__ thr,
                                                         uint32_t *__restrict__ rthr, uint32_t *__restrict__ rw,
+                                                        uint32_t *__restrict__ big, unsigned int *__restrict__ nbig,
                                                         unsigned int *__restrict__ flags) {
+  unsigned int bad = 0;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const uint32_t s = off[v], e = off[v + 1];
+    if (e - s > kSmallRow) {
+      big[atomicAdd(nbig, 1u)] = v;
+      continue;
+    }
+    const uint32_t common0 = e > s ? thr[s] : 0u;
+    const uint32_t w0 = e > s ? __float_as_uint(w[s]) : kPerEdge;
+    bool differs = false, wdiffers = false;
+    uint32_t prev = 0;
+    for (uint32_t i = s; i < e; ++i) {
+      const uint32_t si = src[i];
+      if (thr[i] != common0) differs = true;
+      if (__float_as_uint(w[i]) != w0) wdiffers = true;
+      if (i > s && !(prev < si)) bad |= kGraphNotAscending;
+      prev = si;
+    }
+    rthr[v] = differs ? kPerEdge : common0;
+    rw[v] = wdiffers ? kPerEdge : w0;
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+__global__ void __launch_bounds__(256) prep_big_rows_kernel(const uint32_t *__restrict__ off,
+                                                            const uint32_t *__restrict__ src,
+                                                            const float *__restrict__ w,
+                                                            const uint32_t *__restrict__ thr,
+                                                            uint32_t *__restrict__ rthr, uint32_t *__restrict__ rw,
+                                                            const uint32_t *__restrict__ big,
+                                                            const unsigned int *__restrict__ nbig,
+                                                            unsigned int *__restrict__ flags) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t nb = *nbig;
   unsigned int bad = 0;
-  for (uint32_t v = warp; v < n; v += nwarps) {
+  for (uint32_t b = warp; b < nb; b += nwarps) {
+    const uint32_t v = big[b];
     const uint32_t s = off[v], e = off[v + 1];
     const uint32_t common0 = e > s ? thr[s] : 0u;
     const uint32_t w0 = e > s ? __float_as_uint(w[s]) : kPerEdge;
@@ -184,6 +223,37 @@ __global__ void __launch_bounds__(256) prep_lt_kernel(uint32_t n, const uint32_t
   if (bad) atomicOr(flags, bad);
 }
 
+// Row-parallel check of the uploaded 64-bit offsets (non-decreasing), their
+// narrowing to 32 bits, and the largest in-degree.
+__global__ void prep_offsets_kernel(uint32_t n, const uint64_t *__restrict__ off64, uint32_t *__restrict__ off32,
+                                    unsigned int *__restrict__ info) {
+  uint32_t maxd = 0;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v <= n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t o = off64[v];
+    off32[v] = (uint32_t)o;
+    if (v > 0) {
+      const uint64_t p = off64[v - 1];
+      if (o < p) {
+        atomicOr(info, kGraphBadOffsets);
+        atomicMin(info + 1, (unsigned int)(v - 1));
+      } else {
+        const uint64_t d = o - p;
+        maxd = max(maxd, d > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)d);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxd = max(maxd, __shfl_xor_sync(kFullMask, maxd, o));
+  if ((threadIdx.x & 31u) == 0 && maxd) atomicMax(info + 2, maxd);
+}
+
+cudaError_t launch_offsets_prep(DevGraph &g, unsigned int *info, cudaStream_t s) {
+  int blocks = (int)std::min<uint64_t>(((uint64_t)g.n + 256) / 256, 152ull * 8);
+  if (blocks < 1) blocks = 1;
+  prep_offsets_kernel<<<blocks, 256, 0, s>>>(g.n, g.off64, g.off, info);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_graph_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s) {
   const uint64_t m_pad = (g.m + 3) / 4 * 4 + 4;
   int blocks = (int)std::min<uint64_t>((m_pad + 255) / 256, 152ull * 16);
@@ -191,9 +261,15 @@ cudaError_t launch_graph_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s
   prep_edges_kernel<<<blocks, 256, 0, s>>>(g.n, g.m, m_pad, g.src, g.w, g.thr, d_flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 7) / 8, 152ull * 16);
+  // the uploaded 64-bit offsets are no longer needed: their space holds the big-row list
+  uint32_t *big = reinterpret_cast<uint32_t *>(g.off64);
+  unsigned int *nbig = d_flags + 3;
+  int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 255) / 256, 152ull * 16);
   if (rb < 1) rb = 1;
-  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, g.w, g.thr, g.rthr, g.rw, d_flags);
+  prep_rows_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.src, g.w, g.thr, g.rthr, g.rw, big, nbig, d_flags);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  prep_big_rows_kernel<<<152 * 8, 256, 0, s>>>(g.off, g.src, g.w, g.thr, g.rthr, g.rw, big, nbig, d_flags);
   return cudaGetLastError();
 }
 

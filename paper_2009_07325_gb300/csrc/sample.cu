@@ -557,7 +557,6 @@ constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices p
 constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
 constexpr uint32_t kChunkSG = 256;           // super-groups (4096 in-edges) per chunk of a screened row
 constexpr uint32_t kBigWarps = kBigBlock / 32;
-constexpr int kBigBlocksPerSM = 8;          // register cap that keeps 8 blocks (64 warps) per SM
 constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
 static_assert(kChunkGroups % kStepGroups == 0 && kChunkSG % kStepSG == 0, "a chunk is whole warp steps");
 
