@@ -266,9 +266,13 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t mine, uint32_t &total) {
 // independent Philox chains are in flight per lane.
 constexpr uint32_t kGPL = 2;
 constexpr uint32_t kStepGroups = 32 * kGPL;
-// Super-groups (of 16 in-edges) each lane scans per warp step in a screened row.
+// Super-groups (of 16 in-edges) each lane scans per warp step in a screened
+// row: four in the block-per-set pass, two in the warp-per-set pass (whose
+// per-warp state is larger).
 constexpr uint32_t kSGPL = 4;
 constexpr uint32_t kStepSG = 32 * kSGPL;
+constexpr uint32_t kSGPLCommon = 2;
+constexpr uint32_t kStepSGCommon = 32 * kSGPLCommon;
 
 // Coins of one warp step over groups [base, base + kStepGroups) of the row
 // [s, e) whose last group is glast; lv[q] holds lane group base + 32q + lane.
@@ -322,18 +326,18 @@ __device__ __forceinline__ void resolve_pending(const uint32_t *pe, const uint32
   __syncwarp();
 }
 
-// One warp step over super-groups [base, base + kStepSG) of a screened
+// One warp step over super-groups [base, base + 32 SG) of a screened
 // row [s, e) (threshold rt, last super-group glast): the top bytes of 16
 // coins per call; edges with a zero byte join the pending list.
-template <typename Flush>
+template <uint32_t SG, typename Flush>
 __device__ __forceinline__ void step_screened(uint32_t base, uint32_t glast, uint32_t s, uint32_t e, uint32_t rt,
                                               const CoinKey &ck, uint32_t *pe, uint32_t *pt, uint32_t &npend,
                                               uint32_t *cand, uint32_t &ncand, uint32_t cap, Flush &&flush) {
   const uint32_t lane = lane_id();
-  uint32_t z[kSGPL];
+  uint32_t z[SG];
   uint32_t cnt = 0;
 #pragma unroll
-  for (uint32_t q = 0; q < kSGPL; ++q) {
+  for (uint32_t q = 0; q < SG; ++q) {
     const uint32_t g = base + 32 * q + lane;
     z[q] = g <= glast ? sgroup_zero(g, s, e, ck) : 0u;
     cnt += __popc(z[q]);
@@ -345,7 +349,7 @@ __device__ __forceinline__ void step_screened(uint32_t base, uint32_t glast, uin
   if (total <= kPend) {
     uint32_t pos = npend + excl;
 #pragma unroll
-    for (uint32_t q = 0; q < kSGPL; ++q) {
+    for (uint32_t q = 0; q < SG; ++q) {
       uint32_t m = z[q];
       const uint32_t g = base + 32 * q + lane;
       while (m) {
@@ -366,7 +370,7 @@ __device__ __forceinline__ void step_screened(uint32_t base, uint32_t glast, uin
     uint32_t x = 0;
     bool has = false;
 #pragma unroll
-    for (uint32_t q = 0; q < kSGPL; ++q)
+    for (uint32_t q = 0; q < SG; ++q)
       if (!has && z[q]) {
         const uint32_t i = __ffs(z[q]) - 1;
         z[q] &= z[q] - 1;
@@ -516,8 +520,8 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         if (screened(rt)) {                    // 16 coins per Philox call
           const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
           scanned += 4 * (g1 - g0 + 1);
-          for (uint32_t base = g0; base <= g1 && !overflow; base += kStepSG)
-            step_screened(base, g1, s, e, rt, ck, pe, pt, npend, cand, ncand, kCandCap, flush);
+          for (uint32_t base = g0; base <= g1 && !overflow; base += kStepSGCommon)
+            step_screened<kSGPLCommon>(base, g1, s, e, rt, ck, pe, pt, npend, cand, ncand, kCandCap, flush);
           continue;
         }
         const uint32_t rl = lim(rt);
@@ -695,7 +699,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
           const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkSG;
           const uint32_t c1 = c0 + kChunkSG - 1 < g1 ? c0 + kChunkSG - 1 : g1;
           for (uint32_t base = c0; base <= c1; base += kStepSG)
-            step_screened(base, c1, s, e, rt, ck, pe, pt, npend, cand, ncand, kBigCand, flush);
+            step_screened<kSGPL>(base, c1, s, e, rt, ck, pe, pt, npend, cand, ncand, kBigCand, flush);
           continue;
         }
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
