@@ -617,12 +617,17 @@ def run_ours(args):
     e2e_t, e2e_units = 0.0, 0
     ctx.graph_load(g.n, off_p, src_p, w_p)    # untimed warm-up: the first load allocates the graph arrays
     run_once()
+    e2e_load, e2e_run = [], []
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.graph_load(g.n, off_p, src_p, w_p)
+        t1 = time.perf_counter()
         r = run_once()
-        e2e_t += time.perf_counter() - t0
+        t2 = time.perf_counter()
+        e2e_t += t2 - t0
+        e2e_load.append(1e3 * (t1 - t0))
+        e2e_run.append(1e3 * (t2 - t1))
         e2e_units += r["rr_count"]
     e2e_u, e2e_s = aggregate(float(e2e_units), e2e_t)
     d2h = 4 * k * max(T, 1) + 8 + 8
@@ -648,7 +653,8 @@ def run_ours(args):
             "tuning": {"group_budget": budget, "by": tuned_by},
             "sample_ms_per_step": sample_ms / args.steps, "select_ms_per_step": select_ms / args.steps,
             "e2e": {"value": e2e_u / e2e_s, "unit": "RR-sets/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3))},
+                    "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3)),
+                    "load_ms": e2e_load, "run_ms": e2e_run},
             "gpu_launches": launches,
             "roofline": roofline(kname, coins, calls, alg_bytes, members_total, kern_s, n_launch, philox_calls_per_s,
                                  hbm_peak, peak_kind, traffic, tk["large_launches"]),

@@ -63,7 +63,7 @@ __device__ __forceinline__ unsigned long long lt_round(double P) {
 // common IC threshold (rthr) and the row's common weight (rw: the fp32 bits
 // when every in-edge of the row carries the same weight, else kPerEdge).
 // Rows of at most kSmallRow in-edges take one thread each; the others are
-// listed (big, count in *nbig) for a warp each (prep_big_rows_kernel).
+// listed (big, count in *nbig) for a block each (prep_big_rows_kernel).
 constexpr uint32_t kSmallRow = 64;
 
 __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32_t *__restrict__ off,
@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(uint32_t n, const uint32
   if (bad) atomicOr(flags, bad);
 }
 
+// Block per listed row (more than kSmallRow in-edges): the same checks, 256
+// edges per step, so a hub row of 10^5 in-edges is not left to one warp.
 __global__ void __launch_bounds__(256) prep_big_rows_kernel(const uint32_t *__restrict__ off,
                                                             const uint32_t *__restrict__ src,
                                                             const float *__restrict__ w,
@@ -105,30 +107,23 @@ __global__ void __launch_bounds__(256) prep_big_rows_kernel(const uint32_t *__re
                                                             const uint32_t *__restrict__ big,
                                                             const unsigned int *__restrict__ nbig,
                                                             unsigned int *__restrict__ flags) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t nb = *nbig;
   unsigned int bad = 0;
-  for (uint32_t b = warp; b < nb; b += nwarps) {
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const uint32_t v = big[b];
-    const uint32_t s = off[v], e = off[v + 1];
-    const uint32_t common0 = e > s ? thr[s] : 0u;
-    const uint32_t w0 = e > s ? __float_as_uint(w[s]) : kPerEdge;
+    const uint32_t s = off[v], e = off[v + 1];   // e - s > kSmallRow
+    const uint32_t common0 = thr[s];
+    const uint32_t w0 = __float_as_uint(w[s]);
     bool differs = false, wdiffers = false;
-    for (uint32_t base = s; base < e; base += 32) {
-      const uint32_t i = base + lane;
-      const bool in = i < e;
-      const uint32_t si = in ? src[i] : 0u;
-      if (in && thr[i] != common0) differs = true;
-      if (in && __float_as_uint(w[i]) != w0) wdiffers = true;
-      uint32_t prev = __shfl_up_sync(kFullMask, si, 1);
-      if (lane == 0 && base > s) prev = src[base - 1];
-      if (in && i > s && !(prev < si)) bad |= kGraphNotAscending;
+    for (uint32_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+      const uint32_t si = src[i];
+      if (thr[i] != common0) differs = true;
+      if (__float_as_uint(w[i]) != w0) wdiffers = true;
+      if (i > s && !(src[i - 1] < si)) bad |= kGraphNotAscending;
     }
-    const bool any_diff = __any_sync(kFullMask, differs);
-    const bool any_wdiff = __any_sync(kFullMask, wdiffers);
-    if (lane == 0) {
+    const int any_diff = __syncthreads_or(differs);
+    const int any_wdiff = __syncthreads_or(wdiffers);
+    if (threadIdx.x == 0) {
       rthr[v] = any_diff ? kPerEdge : common0;
       rw[v] = any_wdiff ? kPerEdge : w0;
     }

@@ -173,10 +173,13 @@ constexpr uint32_t kScreenIdx = 0x80000000u;   // group indices of the top bytes
 constexpr uint32_t kResidIdx = 0x40000000u;    // group indices of the residuals (one-word groups stay below 2^30)
 __device__ __forceinline__ bool screened(uint32_t t) { return t - 1u < kScreenMax; }   // 1 <= t <= 2^16
 
-// Bit i of the result is set iff byte i of x is zero (exact per byte).
+// Bit i of the result is set iff byte i of x is zero (exact per byte). The
+// marks at bits 0, 8, 16, 24 of t >> 7 are gathered to bits 24..27 by one
+// multiply (shifts 24, 17, 10, 3; the other partial products land on
+// distinct lower bits, so nothing carries into 24..27).
 __device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
   const uint32_t t = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);   // 0x80 in each zero byte
-  return ((t >> 7) & 1u) | ((t >> 14) & 2u) | ((t >> 21) & 4u) | ((t >> 28) & 8u);
+  return ((t >> 7) * 0x01020408u) >> 24;
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4 &r, uint32_t i) {
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
   __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
   __shared__ uint32_t w_tot[kBigWarps];
   __shared__ unsigned long long s_item, s_base;
-  __shared__ uint32_t s_head, s_tail, s_next;
+  __shared__ uint32_t s_tail, s_next;
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t *cand = cand_all[warp];
   uint32_t *pe = pe_all[warp], *pt = pt_all[warp];
@@ -631,14 +634,14 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       const uint32_t root = draw_root(key, id_lo(V, j), V.rhi, V.n);
       q[0] = root;
       bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
-      s_head = 0;
       s_tail = 1;
     }
     __syncthreads();
     uint32_t ncand = 0, npend = 0;             // this warp's buffered live edges, pending screened edges
     auto flush = [&]() { block_flush(src, cand, ncand, bm, q, qcap, &s_tail); };
+    uint32_t head = 0;                         // frontier vertices expanded (the same in every thread)
     for (;;) {
-      const uint32_t head = s_head, tail = s_tail;
+      const uint32_t tail = s_tail;
       if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
       const uint32_t nb = tail - head < kBatch ? tail - head : kBatch;
       uint32_t nch[kRowsPerThread], mine = 0;  // chunks of this thread's frontier rows
@@ -728,8 +731,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
         ncand = 0;
       }
       __syncthreads();                         // appended vertices visible; batch done
-      if (tid == 0) s_head = head + nb;
-      __syncthreads();
+      head += nb;
     }
     // commit the set: q[0 .. s_tail); a set that outgrew the queue is
     // abandoned (its bits cleared) and handed to a pass with n-entry queues
