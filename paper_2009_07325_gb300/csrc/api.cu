@@ -243,6 +243,7 @@ void gim_destroy(gim_ctx *ctx) {
   mrim_release(ctx);
   if (ctx->owns_graph) free_graph(ctx->g);
   free_graph(ctx->g_spare);
+  dfree(ctx->d_info);
   dfree(ctx->st.members);
   dfree(ctx->st.rr_start);
   dfree(ctx->st.rr_len);
@@ -278,12 +279,10 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   } else {
     free_graph(ctx->g_spare);
   }
-  unsigned int *d_info = nullptr;   // flags, first decreasing row, largest in-degree, big-row count
-  unsigned int info[4] = {0, 0, 0, 0};
+  unsigned int info[4] = {0, 0, 0, 0};   // flags, first decreasing row, largest in-degree, big-row count
   cudaError_t e = cudaSuccess;
   auto bail = [&](cudaError_t err, const char *what) {
     free_graph(g);
-    dfree(d_info);
     return cuda_err(ctx, err, what);
   };
   if (!g.off) {
@@ -299,12 +298,11 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   }
   g.n = n;
   g.m = m;
-  if ((e = cudaMalloc(&d_info, 4 * sizeof(unsigned int))) != cudaSuccess) return bail(e, "alloc flags");
+  if (!ctx->d_info && (e = cudaMalloc(&ctx->d_info, 4 * sizeof(unsigned int))) != cudaSuccess)
+    return bail(e, "alloc flags");
+  unsigned int *d_info = ctx->d_info;
   // a graph that fails validation leaves its arrays for the next load and the context as it was
-  auto reject = [&]() {
-    ctx->g_spare = g;
-    dfree(d_info);
-  };
+  auto reject = [&]() { ctx->g_spare = g; };
   if ((e = cudaMemcpyAsync(g.off64, in_offsets, ((uint64_t)n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return bail(e, "upload offsets");
   if ((e = cudaMemsetAsync(g.src + m, 0, (m_pad - m) * 4, s)) != cudaSuccess) return bail(e, "clear padding");
@@ -339,7 +337,6 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
                    (flags & kGraphNotAscending) ? "sources not strictly ascending within a row; " : "",
                    (flags & kGraphBadWeight) ? "weight outside [0, 1]; " : "");
   }
-  dfree(d_info);
 
   // commit: replace the graph (its arrays are kept for the next load) and empty the collection
   if (ctx->owns_graph && ctx->g.off) {

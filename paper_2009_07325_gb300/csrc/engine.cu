@@ -112,14 +112,13 @@ gim_status ensure_lt(gim_ctx *ctx) {
   DevGraph &g = ctx->g;
   cudaStream_t s = ctx->stream;
   if (!g.cum) CU(cudaMalloc(&g.cum, std::max<uint64_t>(g.m_cap, 1) * 8));
-  unsigned int *d_flags = nullptr;
-  CU(cudaMalloc(&d_flags, 4));
+  if (!ctx->d_info) CU(cudaMalloc(&ctx->d_info, 4 * sizeof(unsigned int)));
+  unsigned int *d_flags = ctx->d_info;
   unsigned int flags = 0;
   cudaError_t e = cudaMemsetAsync(d_flags, 0, 4, s);
   if (e == cudaSuccess) e = launch_lt_prep(g, d_flags, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_flags, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_flags);
   if (e != cudaSuccess) return cuda_err(ctx, e, "LT thresholds");
   ctx->launches++;
   ctx->lt_ok = (flags & kGraphNotLT) ? 0 : 1;

@@ -456,6 +456,7 @@ struct gim_ctx {
   uint32_t max_indeg = 0;         // of the loaded graph (degree profile of the autotuner)
   gim::DevGraph g;
   gim::DevGraph g_spare;          // the arrays of the previous graph, reused by the next load that fits
+  unsigned int *d_info = nullptr;  // 4 device words for the graph checks (kept across loads)
 
   // RR collection
   int model = -1;

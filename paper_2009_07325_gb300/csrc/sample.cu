@@ -192,20 +192,35 @@ __device__ __forceinline__ bool resid_live(uint32_t x, uint32_t t, const CoinKey
   return ((word_of(h, (x >> 1) & 3u) >> ((x & 1u) << 4)) & 0xFFFFu) < t;
 }
 
+// 0x80 in each zero byte of x, 0 elsewhere (exact per byte).
+__device__ __forceinline__ uint32_t zero_marks(uint32_t x) {
+  return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+}
+
+// Spreads bits 0..3 of a nibble to bits 0, 8, 16, 24 (one multiply; the
+// other partial products land on distinct bits outside the mask).
+__device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+
 // First part of the coins of super-group sg (in-edges 16sg .. 16sg+15) of
-// the row [s, e): bit i is set iff edge 16sg+i lies in the row and its top
+// the row [s, e), in a transposed layout: bit 8b + w is set iff edge
+// 16sg + 4w + b (byte b of word w of the draw) lies in the row and its top
 // byte is zero, i.e. its coin depends on its residual (resid_live).
 __device__ __forceinline__ uint32_t sgroup_zero(uint32_t sg, uint32_t s, uint32_t e, const CoinKey &ck) {
   const uint4 r = coin_words(kScreenIdx | sg, ck);
-  uint32_t z = zero_bytes(r.x) | (zero_bytes(r.y) << 4) | (zero_bytes(r.z) << 8) | (zero_bytes(r.w) << 12);
+  uint32_t z = (zero_marks(r.x) >> 7) | (zero_marks(r.y) >> 6) | (zero_marks(r.z) >> 5) | (zero_marks(r.w) >> 4);
   const uint32_t e0 = sg << 4;                // s - 15 <= e0 <= e - 1
   if (e0 < s || e0 + 16 > e) {
     const uint32_t lo = s > e0 ? s - e0 : 0u;
     const uint32_t hi = e - e0 < 16u ? e - e0 : 16u;
-    z &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+    const uint32_t m = ((1u << hi) - 1u) & ~((1u << lo) - 1u);   // bit 4w + b: edge in the row
+    z &= spread4(m & 0xFu) | (spread4((m >> 4) & 0xFu) << 1) | (spread4((m >> 8) & 0xFu) << 2) |
+         (spread4(m >> 12) << 3);
   }
   return z;
 }
+
+// In-super-group index 4w + b of bit p = 8b + w of a transposed mask.
+__device__ __forceinline__ uint32_t zero_edge(uint32_t p) { return ((p & 7u) << 2) + (p >> 3); }
 
 // Coins of group grp (in-edges 4grp .. 4grp+3) for the row [s, e): bit qi is
 // set iff edge 4grp+qi lies in the row and is live. One Philox call yields
@@ -356,9 +371,9 @@ __device__ __forceinline__ void step_screened(uint32_t base, uint32_t glast, uin
       uint32_t m = z[q];
       const uint32_t g = base + 32 * q + lane;
       while (m) {
-        const uint32_t i = __ffs(m) - 1;
+        const uint32_t p = __ffs(m) - 1;
         m &= m - 1;
-        pe[pos] = (g << 4) + i;
+        pe[pos] = (g << 4) + zero_edge(p);
         pt[pos] = rt;
         ++pos;
       }
@@ -375,9 +390,9 @@ __device__ __forceinline__ void step_screened(uint32_t base, uint32_t glast, uin
 #pragma unroll
     for (uint32_t q = 0; q < SG; ++q)
       if (!has && z[q]) {
-        const uint32_t i = __ffs(z[q]) - 1;
+        const uint32_t p = __ffs(z[q]) - 1;
         z[q] &= z[q] - 1;
-        x = ((base + 32 * q + lane) << 4) + i;
+        x = ((base + 32 * q + lane) << 4) + zero_edge(p);
         has = true;
       }
     if (__ballot_sync(kFullMask, has) == 0u) break;
@@ -617,7 +632,21 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
   uint32_t *q = bs.queue + (uint64_t)blockIdx.x * qcap;
 
   for (;;) {
-    if (tid == 0) s_item = atomicAdd(&L.ctl->next, 1ull);
+    // thread 0 takes the next set and plants its root (the previous set ended
+    // with a barrier, so the queue and bitmap are free); one barrier publishes both
+    if (tid == 0) {
+      const unsigned long long it = atomicAdd(&L.ctl->next, 1ull);
+      s_item = it;
+      if (it < L.total_items) {
+        uint32_t i0;
+        uint64_t j0;
+        const InstView V0 = item_view<kOne>(L, one, it, i0, j0);
+        const uint32_t root = draw_root(V0.key, id_lo(V0, j0), V0.rhi, V0.n);
+        q[0] = root;
+        bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
+        s_tail = 1;
+      }
+    }
     __syncthreads();
     const unsigned long long item = s_item;
     if (item >= L.total_items) break;
@@ -630,13 +659,6 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
     const uint32_t *__restrict__ src = V.src;
     const PhiloxKey key = V.key;
     const CoinKey ck = coin_key(id_lo(V, j), V.jhi, key);
-    if (tid == 0) {
-      const uint32_t root = draw_root(key, id_lo(V, j), V.rhi, V.n);
-      q[0] = root;
-      bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
-      s_tail = 1;
-    }
-    __syncthreads();
     uint32_t ncand = 0, npend = 0;             // this warp's buffered live edges, pending screened edges
     auto flush = [&]() { block_flush(src, cand, ncand, bm, q, qcap, &s_tail); };
     uint32_t head = 0;                         // frontier vertices expanded (the same in every thread)
