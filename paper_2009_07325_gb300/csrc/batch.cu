@@ -81,12 +81,6 @@ __device__ __forceinline__ uint32_t owner(const SelDesc *d, uint32_t ni, uint64_
   return lo;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
-  return v;
-}
-
 __device__ __forceinline__ unsigned long long warp_incl_u64(unsigned long long v) {
   const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll

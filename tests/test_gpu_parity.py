@@ -219,6 +219,39 @@ def test_screened_coins_bit_exact(budget):
         ctx.close()
 
 
+def test_graph_reloads_lazy_lt_and_offset_errors():
+    """Graphs loaded one after another reuse the previous graph's arrays (a
+    smaller graph, then the first again); the LT thresholds are built on the
+    first LT use, after IC work on the same graph; decreasing offsets are
+    rejected with their row and leave the context as it was."""
+    a = I.wc_weights(I.er(2000, 20000, 1))
+    b = I.wc_weights(I.er(500, 3000, 4))
+    ctx = Context(0)
+    for g in (a, b, a, b, a):
+        ctx.load(g)
+        ctx.sample_rr(GIM_IC, 3000, 5)
+        orc = O.Oracle(g)
+        orc.sample(GIM_IC, 5, 3000, THREADS)
+        _same_collection(ctx, orc)
+        # LT after IC work: thresholds built now, from the weights kept on the device
+        ctx.reset_rr()
+        ctx.sample_rr(GIM_LT, 2000, 6)
+        olt = O.Oracle(g)
+        olt.sample(GIM_LT, 6, 2000, THREADS)
+        _same_collection(ctx, olt)
+        assert ctx.lt_valid
+    off = a.offsets.copy()
+    off[7], off[8] = off[8], off[7]          # row 7 now ends before it starts
+    assert off[7] > off[8]
+    bad_row = 7
+    with pytest.raises(GimError, match=f"row {bad_row}"):
+        ctx.graph_load(a.n, off, a.sources, a.weights)
+    olt = O.Oracle(a)
+    olt.sample(GIM_LT, 6, 2000, THREADS)
+    _same_collection(ctx, olt)               # the previous graph and collection are intact
+    ctx.close()
+
+
 def test_degenerate_weights_and_sizes():
     base = I.er(300, 1500, 2)
     for p in (0.0, 1.0):
