@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) prep_big_rows_kernel(const uint32_t *__re
   if (bad) atomicOr(flags, bad);
 }
 
-// Warp per row, on the first LT use of the graph: the LT thresholds
+// On the first LT use of the graph, per row: the LT thresholds
 //   cum[e_i] = min(2^32, round_half_up(P_i * 2^32)),
 // P_i the fp64 running sum of the row's weights in CSR order; a row summing
 // to within 1e-6 of 1 gets cum[last] = 2^32 so that it always selects an
@@ -140,80 +140,161 @@ __global__ void __launch_bounds__(256) prep_big_rows_kernel(const uint32_t *__re
 // the row's non-zero weights, every weight is an integer q_t times 2^E; when
 // all prefix sums of the q_t stay below 2^53, every fp64 partial sum is
 // representable, so the sequential fp64 additions never round and P_i equals
-// the integer prefix sum times 2^E, which the warp computes with a parallel
-// scan. Other rows (weights spanning more than 2^39, or huge sums) take the
-// strictly sequential fp64 loop. Both give the same P_i.
+// the integer prefix sum Q_i times 2^E. Then P_i * 2^32 = Q_i * 2^(E+32) is
+// rounded half up in integer arithmetic (lt_round_int). Other rows (weights
+// spanning more than 2^29 ulps, or huge sums) take the strictly sequential
+// fp64 loop (lt_round). Both give the same thresholds. Rows of at most
+// kSmallRow in-edges take one thread each (prep_lt_kernel); the others are
+// listed for a block each (prep_lt_big_kernel), which scans 256 in-edges
+// at a time.
+
+// round_half_up(Q * 2^k), clamped to 2^32, for Q < 2^53.
+__device__ __forceinline__ unsigned long long lt_round_int(unsigned long long Q, int k) {
+  unsigned long long c;
+  if (k >= 0)
+    c = Q << k;                                   // k <= 9 for weights <= 1: no overflow
+  else if (k < -60)
+    c = 0ull;                                     // Q * 2^k < 2^-7
+  else
+    c = (Q + (1ull << (-k - 1))) >> (-k);
+  return c > 4294967296ull ? 4294967296ull : c;
+}
+
+// The row fix-ups and the LT-validity flag from the row total P.
+__device__ __forceinline__ void lt_row_end(double P, uint32_t s, uint32_t e, uint64_t *cum, unsigned int &bad) {
+  if (e > s && fabs(__dsub_rn(P, 1.0)) <= 1e-6) cum[e - 1] = 4294967296ull;
+  if (P > 1.0 + 1e-6) bad |= kGraphNotLT;
+}
+
+// Sequential fp64 prefix sums of the row (the fallback): returns P.
+__device__ __forceinline__ double lt_row_sequential(const float *__restrict__ w, uint64_t *cum, uint32_t s, uint32_t e) {
+  double P = 0.0;
+  for (uint32_t i = s; i < e; ++i) {
+    P = __dadd_rn(P, (double)w[i]);
+    cum[i] = lt_round(P);
+  }
+  return P;
+}
+
 __global__ void __launch_bounds__(256) prep_lt_kernel(uint32_t n, const uint32_t *__restrict__ off,
                                                       const float *__restrict__ w, uint64_t *__restrict__ cum,
+                                                      uint32_t *__restrict__ big, unsigned int *__restrict__ nbig,
                                                       unsigned int *__restrict__ flags) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned int bad = 0;
-  for (uint32_t v = warp; v < n; v += nwarps) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const uint32_t s = off[v], e = off[v + 1];
-    int emin = 0x7FFFFFFF;
-    for (uint32_t i = s + lane; i < e; i += 32) {   // smallest ulp exponent
-      uint32_t mant;
-      emin = min(emin, ulp_exponent(w[i], &mant));
+    if (e - s > kSmallRow) {
+      big[atomicAdd(nbig, 1u)] = v;
+      continue;
     }
+    int emin = 0x7FFFFFFF;
+    uint32_t mant;
+    for (uint32_t i = s; i < e; ++i) emin = min(emin, ulp_exponent(w[i], &mant));
+    double P = 0.0;
+    if (emin == 0x7FFFFFFF) {
+      for (uint32_t i = s; i < e; ++i) cum[i] = 0ull;   // all weights zero
+    } else {
+      bool exact = true;
+      unsigned long long Q = 0;
+      for (uint32_t i = s; i < e && exact; ++i) {
+        const int ex = ulp_exponent(w[i], &mant);
+        if (ex != 0x7FFFFFFF) {
+          const int sh = ex - emin;
+          if (sh > 29) {
+            exact = false;                               // q would reach 2^53
+            break;
+          }
+          Q += (unsigned long long)mant << sh;
+          if (Q >= (1ull << 53)) {
+            exact = false;
+            break;
+          }
+        }
+        cum[i] = lt_round_int(Q, emin + 32);
+      }
+      P = exact ? __dmul_rn(__ull2double_rn(Q), __longlong_as_double((long long)(emin + 1023) << 52))
+                : lt_row_sequential(w, cum, s, e);
+    }
+    lt_row_end(P, s, e, cum, bad);
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+__global__ void __launch_bounds__(256) prep_lt_big_kernel(const uint32_t *__restrict__ off,
+                                                          const float *__restrict__ w, uint64_t *__restrict__ cum,
+                                                          const uint32_t *__restrict__ big,
+                                                          const unsigned int *__restrict__ nbig,
+                                                          unsigned int *__restrict__ flags) {
+  __shared__ int s_min[8];
+  __shared__ unsigned long long s_tot[8];
+  __shared__ double s_P;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+  const uint32_t nb = *nbig;
+  unsigned int bad = 0;
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint32_t v = big[b];
+    const uint32_t s = off[v], e = off[v + 1];
+    uint32_t mant;
+    int emin = 0x7FFFFFFF;
+    for (uint32_t i = s + tid; i < e; i += 256) emin = min(emin, ulp_exponent(w[i], &mant));
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) emin = min(emin, __shfl_xor_sync(kFullMask, emin, d));
-    // exact parallel prefix sums when no fp64 addition can round
+    if (lane == 0) s_min[wid] = emin;
+    __syncthreads();
+    emin = s_min[0];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) emin = min(emin, s_min[t]);
     bool exact = true;
     unsigned long long carry = 0;
-    double scale = 1.0;
     if (emin == 0x7FFFFFFF) {
-      for (uint32_t i = s + lane; i < e; i += 32) cum[i] = 0ull;      // all weights zero
+      for (uint32_t i = s + tid; i < e; i += 256) cum[i] = 0ull;
     } else {
-      scale = __longlong_as_double((long long)(emin + 1023) << 52);   // 2^emin, emin >= -149
-      for (uint32_t base = s; base < e && exact; base += 32) {
-        const uint32_t i = base + lane;
+      for (uint32_t base = s; base < e; base += 256) {
+        const uint32_t i = base + tid;
         unsigned long long q = 0;
         bool ok = true;
         if (i < e) {
-          uint32_t mant;
           const int ex = ulp_exponent(w[i], &mant);
           if (ex != 0x7FFFFFFF) {
             const int sh = ex - emin;
-            if (sh > 29) ok = false;                      // q would reach 2^53
+            if (sh > 29) ok = false;
             else q = (unsigned long long)mant << sh;
           }
         }
-        if (!__all_sync(kFullMask, ok)) {
+        if (!__syncthreads_and(ok)) {
           exact = false;
           break;
         }
-        const unsigned long long incl = warp_incl_scan_u64(q) + carry;
-        carry = __shfl_sync(kFullMask, incl, 31);
-        if (carry >= (1ull << 53)) {
+        const unsigned long long wincl = warp_incl_scan_u64(q);
+        if (lane == 31) s_tot[wid] = wincl;
+        __syncthreads();
+        unsigned long long before = carry, total = carry;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if ((uint32_t)t < wid) before += s_tot[t];
+          total += s_tot[t];
+        }
+        __syncthreads();                              // s_tot is rewritten by the next chunk
+        if (total >= (1ull << 53)) {                  // the same decision in every thread
           exact = false;
           break;
         }
-        if (i < e) cum[i] = lt_round(__dmul_rn(__ull2double_rn(incl), scale));
+        if (i < e) cum[i] = lt_round_int(before + wincl, emin + 32);
+        carry = total;
       }
     }
     double P = 0.0;
-    if (exact) {
-      P = __dmul_rn(__ull2double_rn(carry), scale);
+    if (emin == 0x7FFFFFFF) {
+      P = 0.0;
+    } else if (exact) {
+      P = __dmul_rn(__ull2double_rn(carry), __longlong_as_double((long long)(emin + 1023) << 52));
     } else {
-      // sequential fp64: every lane adds the broadcast weights in CSR order
-      for (uint32_t base = s; base < e; base += 32) {
-        const uint32_t i = base + lane;
-        const float wi = i < e ? w[i] : 0.0f;
-        const uint32_t cnt = e - base < 32u ? e - base : 32u;
-        double mine = 0.0;
-        for (uint32_t t = 0; t < cnt; ++t) {
-          P = __dadd_rn(P, (double)__shfl_sync(kFullMask, wi, t));
-          if (t == lane) mine = P;
-        }
-        if (i < e) cum[i] = lt_round(mine);
-      }
+      if (tid == 0) s_P = lt_row_sequential(w, cum, s, e);
+      __syncthreads();
+      P = s_P;
     }
-    if (lane == 0) {
-      if (e > s && fabs(__dsub_rn(P, 1.0)) <= 1e-6) cum[e - 1] = 4294967296ull;
-      if (P > 1.0 + 1e-6) bad |= kGraphNotLT;
-    }
+    if (tid == 0) lt_row_end(P, s, e, cum, bad);
+    __syncthreads();                                  // shared words are reused by the next row
   }
   if (bad) atomicOr(flags, bad);
 }
@@ -269,9 +350,17 @@ cudaError_t launch_graph_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s
 }
 
 cudaError_t launch_lt_prep(DevGraph &g, unsigned int *d_flags, cudaStream_t s) {
-  int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 7) / 8, 152ull * 16);
+  // the uploaded 64-bit offsets are no longer needed: their space holds the big-row list
+  uint32_t *big = reinterpret_cast<uint32_t *>(g.off64);
+  unsigned int *nbig = d_flags + 3;
+  cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  int rb = (int)std::min<uint64_t>(((uint64_t)g.n + 255) / 256, 152ull * 16);
   if (rb < 1) rb = 1;
-  prep_lt_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.w, g.cum, d_flags);
+  prep_lt_kernel<<<rb, 256, 0, s>>>(g.n, g.off, g.w, g.cum, big, nbig, d_flags);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  prep_lt_big_kernel<<<152 * 8, 256, 0, s>>>(g.off, g.w, g.cum, big, nbig, d_flags);
   return cudaGetLastError();
 }
 
