@@ -142,6 +142,8 @@ gim_status shared_acquire(gim_ctx *ctx) {
     CU(cudaMemset(D.cs.hash, 0, (uint64_t)workers * kHashSlots * 8));
     CU(cudaMemset(D.cs.epoch, 0, (uint64_t)workers * 4));
     CU(cudaMalloc(&D.d_ctl, sizeof(SampleCtl)));
+    CU(cudaMalloc(&D.lt_ovf, (uint64_t)kLtOvfSlots * kLtGroupPath * sizeof(uint32_t)));
+    CU(cudaMalloc(&D.d_ovf_next, sizeof(unsigned int)));
     CU(cudaMallocHost(&D.h_ctl, sizeof(SampleCtl)));
     D.lt_grid = (uint32_t)ctx->sm_count * (uint32_t)lt_common_blocks_per_sm();
   }
@@ -166,7 +168,10 @@ void shared_release(int device) {
   D.h_desc = nullptr;
   D.h_desc_cap = 0;
   dfree(D.d_def);
+  dfree(D.d_defslot);
   D.def_cap = 0;
+  dfree(D.lt_ovf);
+  dfree(D.d_ovf_next);
   dfree(D.d_ctl);
   if (D.h_ctl) cudaFreeHost(D.h_ctl);
   D.h_ctl = nullptr;
@@ -217,8 +222,10 @@ gim_status ensure_lists(gim_ctx *ctx, DeviceShared &D, uint64_t n_inst, uint64_t
   }
   if (D.def_cap < 2 * items) {
     dfree(D.d_def);
+    dfree(D.d_defslot);
     D.def_cap = 0;
     CU(cudaMalloc(&D.d_def, 2 * items * sizeof(unsigned long long)));
+    CU(cudaMalloc(&D.d_defslot, 2 * items * sizeof(uint32_t)));
     D.def_cap = 2 * items;
   }
   return GIM_OK;
@@ -270,6 +277,8 @@ struct Pass {
   uint64_t items;
   const unsigned long long *list;
   unsigned long long *out;
+  const uint32_t *list_slots;   // overflow slots of list (nullable)
+  uint32_t *out_slots;          // overflow slots of out
 };
 
 // Runs one launch over the group's descriptors and settles every store.
@@ -296,6 +305,11 @@ gim_status run_one(gim_ctx *ctx, DeviceShared &D, int model, std::vector<SampleJ
   L.deferred_cap = D.def_cap / 2;
   L.ctl = D.d_ctl;
   L.group_budget = P.large ? 0xFFFFFFFFu : ctx->group_budget;   // the first context's knob serves the launch
+  L.item_slots = P.list_slots;
+  L.deferred_slots = P.out_slots;
+  L.lt_ovf = D.lt_ovf;
+  L.lt_ovf_next = D.d_ovf_next;
+  L.lt_ovf_cap = kLtOvfSlots;
   if (used) *used = L;
   CU(cudaEventRecord(ctx->ev[6], s));
   cudaError_t e;
@@ -392,7 +406,9 @@ gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s) {
       }
     };
     unsigned long long *list_a = D.d_def, *list_b = D.d_def + D.def_cap / 2;
-    Pass P{false, total, nullptr, list_a};
+    uint32_t *slot_a = D.d_defslot, *slot_b = D.d_defslot + D.def_cap / 2;
+    CU(cudaMemsetAsync(D.d_ovf_next, 0, sizeof(unsigned int), s));   // saved LT paths of this call
+    Pass P{false, total, nullptr, list_a, nullptr, slot_a};
     if ((st = run_one(ctx, D, model, grp, P, s, &L0)) != GIM_OK) return rollback(), st;
     uint64_t pending = D.h_ctl->n_deferred;
     int rounds = 0;
@@ -404,10 +420,11 @@ gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s) {
       // first with capped queues (more sets in flight); what is still pending
       // after that (a set beyond kSlotQueue members, or a full store) gets n
       if ((st = ensure_big(ctx, D, nmax, rounds > 1)) != GIM_OK) return rollback(), st;
-      Pass Q{true, pending, list_a, list_b};
+      Pass Q{true, pending, list_a, list_b, slot_a, slot_b};
       if ((st = run_one(ctx, D, model, grp, Q, s, nullptr)) != GIM_OK) return rollback(), st;
       pending = D.h_ctl->n_deferred;
       std::swap(list_a, list_b);
+      std::swap(slot_a, slot_b);
     }
     for (auto *jb : grp) {
       jb->ctx->R += jb->count;

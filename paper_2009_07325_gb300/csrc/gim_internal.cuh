@@ -185,7 +185,19 @@ struct SampleLaunch {
   unsigned long long deferred_cap;
   SampleCtl *ctl;
   uint32_t group_budget;             // common pass: edge groups (4 in-edges) a set may scan
+  // LT walks that outgrow the common pass's path keep it in an overflow slot
+  // (kLtGroupPath entries) so that the large pass continues them instead of
+  // starting over: items[i] / deferred[d] have slot item_slots[i] /
+  // deferred_slots[d] (kNoSlot: none)
+  const uint32_t *item_slots;        // nullable
+  uint32_t *deferred_slots;          // nullable
+  uint32_t *lt_ovf;                  // lt_ovf_cap slots of kLtGroupPath vertices
+  unsigned int *lt_ovf_next;         // slots handed out in this sampling call
+  uint32_t lt_ovf_cap;
 };
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+constexpr uint32_t kLtGroupPath = 512;     // LT common pass: path entries per walk (shared memory)
+constexpr uint32_t kLtOvfSlots = 8192;     // LT walks continued from a saved path per sampling call
 
 constexpr uint32_t kQueueCap = 4096;        // common pass: members per set before it is deferred
 constexpr uint32_t kHashBits = 13;
@@ -330,7 +342,10 @@ struct DeviceShared {
   InstDesc *h_desc = nullptr;          // pinned
   uint64_t h_desc_cap = 0;
   unsigned long long *d_def = nullptr; // two deferred-set lists
+  uint32_t *d_defslot = nullptr;       // their overflow slots (same layout)
   uint64_t def_cap = 0;
+  uint32_t *lt_ovf = nullptr;          // kLtOvfSlots saved LT paths
+  unsigned int *d_ovf_next = nullptr;
   SampleCtl *d_ctl = nullptr;
   SampleCtl *h_ctl = nullptr;          // pinned
 };

@@ -117,12 +117,14 @@ __device__ __forceinline__ InstView item_view(const SampleLaunch &L, const InstD
   return view_of(L.inst[ii]);
 }
 
-__device__ __forceinline__ void defer(const SampleLaunch &L, uint32_t ii, uint64_t j) {
+__device__ __forceinline__ void defer(const SampleLaunch &L, uint32_t ii, uint64_t j, uint32_t slot = kNoSlot) {
   const unsigned long long d = atomicAdd(&L.ctl->n_deferred, 1ull);
-  if (d < L.deferred_cap)
+  if (d < L.deferred_cap) {
     L.deferred[d] = ((unsigned long long)ii << 32) | (uint32_t)j;
-  else
+    if (L.deferred_slots) L.deferred_slots[d] = slot;
+  } else {
     atomicOr(&L.ctl->err, kErrDeferredFull);
+  }
 }
 
 // Warp-wide: copies the finished set q[0..size) to instance ii's store and
@@ -886,12 +888,24 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     const PhiloxKey key = V.key;
     const uint32_t jlo = id_lo(V, j), jhi = V.jhi;
     uint32_t x = draw_root(key, id_lo(V, j), V.rhi, V.n);
-    if (lane == 0) {
+    uint32_t len = 1;
+    const uint32_t slot = (kLarge && L.item_slots) ? L.item_slots[item] : kNoSlot;
+    if (kLarge && slot < L.lt_ovf_cap && cap >= kLtGroupPath) {
+      // continue a walk from the kLtGroupPath vertices it had reached (the
+      // walk is a function of the vertex sequence, so it resumes exactly)
+      const uint32_t *saved = L.lt_ovf + (uint64_t)slot * kLtGroupPath;
+      for (uint32_t i = lane; i < kLtGroupPath; i += 32) {
+        const uint32_t p = saved[i];
+        path[i] = p;
+        atomicOr(&bm[p >> 5], 1u << (p & 31u));
+      }
+      len = kLtGroupPath;
+      x = saved[kLtGroupPath - 1];
+    } else if (lane == 0) {
       path[0] = x;
       if (kLarge) bm[x >> 5] = 1u << (x & 31u);
     }
     __syncwarp();
-    uint32_t len = 1;
     bool overflow = false;
     for (;;) {
       const uint32_t s = off[x], e = off[x + 1], wb = rw[x];
@@ -946,7 +960,6 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
 // than the path buffer are handed to the large pass.
 constexpr uint32_t kLtLanes = 8;
 constexpr uint32_t kLtWalks = 32 / kLtLanes;
-constexpr uint32_t kLtGroupPath = 512;
 constexpr uint32_t kLtMultiWarps = 8;   // warps per block
 
 __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaunch L) {
@@ -1110,7 +1123,18 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
         }
       }
     }
-    if (active && overflow && gl == 0) defer(L, ii, j);
+    if (active && overflow) {
+      // save the path so that the large pass continues the walk
+      uint32_t slot = kNoSlot;
+      if (gl == 0 && L.lt_ovf) {
+        slot = atomicAdd(L.lt_ovf_next, 1u);
+        if (slot >= L.lt_ovf_cap) slot = kNoSlot;
+      }
+      slot = __shfl_sync(0xFFu << lead, slot, lead);
+      if (slot != kNoSlot)
+        for (uint32_t i = gl; i < kLtGroupPath; i += kLtLanes) L.lt_ovf[(uint64_t)slot * kLtGroupPath + i] = path[i];
+      if (gl == 0) defer(L, ii, j, slot);
+    }
     if (active && ended) active = false;
     __syncwarp();
   }
