@@ -29,7 +29,7 @@
 //   epoch, so it is never cleared. A set that outgrows the queue or scans
 //   more than its edge budget is abandoned and deferred.
 // IC, large-set pass: one 256-thread block per deferred set, with an n-bit
-//   visited bitmap and a queue. Each batch of up to 512 frontier
+//   visited bitmap and a queue. Each batch of up to 256 frontier
 //   vertices is cut into chunks of at most 2048 in-edges (512 Philox calls),
 //   or 4096 in a super-group row (256 calls), that the block's
 //   warps take from a shared counter, so the heavy tail of huge RR sets is
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 // ---------------------------------------------------------------------------
 // IC large-set pass: one block of kBigBlock threads per RR set.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kRowsPerThread = 2;       // frontier rows each thread loads per block step
+constexpr uint32_t kRowsPerThread = 1;       // frontier rows each thread loads per block step
 constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step
 constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
 constexpr uint32_t kChunkSG = 256;           // super-groups (4096 in-edges) per chunk of a screened row
