@@ -196,8 +196,8 @@ struct SampleLaunch {
   uint32_t lt_ovf_cap;
 };
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
-constexpr uint32_t kLtGroupPath = 512;     // LT common pass: path entries per walk (shared memory)
-constexpr uint32_t kLtOvfSlots = 8192;     // LT walks continued from a saved path per sampling call
+constexpr uint32_t kLtGroupPath = 384;     // LT common pass: path entries per walk (shared memory)
+constexpr uint32_t kLtOvfSlots = 16384;     // LT walks continued from a saved path per sampling call
 
 constexpr uint32_t kQueueCap = 4096;        // common pass: members per set before it is deferred
 constexpr uint32_t kHashBits = 13;
