@@ -202,7 +202,6 @@ constexpr uint32_t kLtOvfSlots = 16384;     // LT walks continued from a saved p
 constexpr uint32_t kQueueCap = 4096;        // common pass: members per set before it is deferred
 constexpr uint32_t kHashBits = 13;
 constexpr uint32_t kHashSlots = 1u << kHashBits;   // common pass: visited hash slots per worker
-constexpr uint32_t kLtPathCap = 1024;       // LT common pass: path length kept in shared memory
 
 // Scratch of the common (warp per set) IC pass; independent of n.
 struct CommonScratch {

@@ -859,16 +859,13 @@ __device__ __forceinline__ uint32_t lt_choose(const uint64_t *__restrict__ cum, 
   return a;
 }
 
-// kLarge = false keeps the path in shared memory (kLtPathCap per warp) and
-// tests "already visited" by a warp-wide compare against the path; kLarge =
-// true is one warp per block with the slot's bitmap and n-entry queue.
-template <bool kLarge>
-__global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, BigScratch bs) {
-  extern __shared__ uint32_t smem[];
+// LT large pass: one warp per block and walk, with the slot's bitmap as the
+// visited set and its queue as the path (walks the common pass deferred).
+__global__ void __launch_bounds__(32) lt_large_kernel(SampleLaunch L, BigScratch bs) {
   const uint32_t lane = lane_id();
-  const uint32_t cap = kLarge ? bs.q_cap : kLtPathCap;
-  uint32_t *bm = kLarge ? bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot : nullptr;
-  uint32_t *path = kLarge ? bs.queue + (uint64_t)blockIdx.x * bs.q_cap : smem + (threadIdx.x >> 5) * kLtPathCap;
+  const uint32_t cap = bs.q_cap;
+  uint32_t *bm = bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot;
+  uint32_t *path = bs.queue + (uint64_t)blockIdx.x * bs.q_cap;
 
   for (;;) {
     unsigned long long item = 0;
@@ -889,8 +886,8 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
     const uint32_t jlo = id_lo(V, j), jhi = V.jhi;
     uint32_t x = draw_root(key, id_lo(V, j), V.rhi, V.n);
     uint32_t len = 1;
-    const uint32_t slot = (kLarge && L.item_slots) ? L.item_slots[item] : kNoSlot;
-    if (kLarge && slot < L.lt_ovf_cap && cap >= kLtGroupPath) {
+    const uint32_t slot = L.item_slots ? L.item_slots[item] : kNoSlot;
+    if (slot < L.lt_ovf_cap && cap >= kLtGroupPath) {
       // continue a walk from the kLtGroupPath vertices it had reached (the
       // walk is a function of the vertex sequence, so it resumes exactly)
       const uint32_t *saved = L.lt_ovf + (uint64_t)slot * kLtGroupPath;
@@ -903,7 +900,7 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
       x = saved[kLtGroupPath - 1];
     } else if (lane == 0) {
       path[0] = x;
-      if (kLarge) bm[x >> 5] = 1u << (x & 31u);
+      bm[x >> 5] = 1u << (x & 31u);
     }
     __syncwarp();
     bool overflow = false;
@@ -914,20 +911,13 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
       uint32_t u = 0;
       const uint32_t a = lt_choose(cum, src, s, e, wb, U, u);
       if (a >= e) break;
-      bool seen;
-      if (kLarge) {
-        uint32_t old = 0;
-        if (lane == 0) old = atomicOr(&bm[u >> 5], 1u << (u & 31u));
-        seen = (__shfl_sync(kFullMask, old, 0) >> (u & 31u)) & 1u;
-      } else {
-        bool hit = false;
-        for (uint32_t i = lane; i < len; i += 32) hit |= (path[i] == u);
-        seen = __any_sync(kFullMask, hit);
-      }
+      uint32_t old = 0;
+      if (lane == 0) old = atomicOr(&bm[u >> 5], 1u << (u & 31u));
+      const bool seen = (__shfl_sync(kFullMask, old, 0) >> (u & 31u)) & 1u;
       if (seen) break;
       if (len == cap) {
         overflow = true;
-        if (kLarge && lane == 0) atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));
+        if (lane == 0) atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));
         break;
       }
       if (lane == 0) path[len] = u;
@@ -936,10 +926,8 @@ __global__ void __launch_bounds__(kLarge ? 32 : 256) lt_kernel(SampleLaunch L, B
       x = u;
     }
     if (overflow) {
-      if (kLarge) {
-        for (uint32_t i = lane; i < len; i += 32) bm[path[i] >> 5] = 0u;
-        __syncwarp();
-      }
+      for (uint32_t i = lane; i < len; i += 32) bm[path[i] >> 5] = 0u;
+      __syncwarp();
       if (lane == 0) defer(L, ii, j);
       continue;
     }
@@ -1220,7 +1208,7 @@ cudaError_t launch_lt_common(const SampleLaunch &L, uint32_t grid, cudaStream_t 
 }
 
 cudaError_t launch_lt_large(const SampleLaunch &L, const BigScratch &bs, uint32_t grid, cudaStream_t s) {
-  lt_kernel<true><<<grid, 32, 0, s>>>(L, bs);
+  lt_large_kernel<<<grid, 32, 0, s>>>(L, bs);
   return cudaGetLastError();
 }
 
