@@ -1,0 +1,71 @@
+"""CPU checks of the benchmark's work accounting (the roofline numerators).
+
+* Philox calls per expanded vertex: indeg/4 for a row with p > 2^-8, and
+  indeg/16 + indeg/256 for a row with p <= 2^-8 (the boundary p = 2^-8 is a
+  16-coin row, as in the coin reading), weighted by occurrence counts.
+* The row probability of a weighted-cascade graph is 1/indeg(v) in fp32, 1
+  for rows without in-edges.
+* The roofline line: achieved = work / time, frac = achieved / peak, in the
+  stated units; the selection roofline divides the library's byte count by
+  the selection kernels' time.
+* Every workload name resolves to a graph recipe and every sweep point to a
+  workload.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bench
+from paper_2009_07325_gb300 import inputs as I
+
+
+def test_philox_calls_per_row_kind():
+    indeg = np.array([4, 255, 256, 1024, 0], np.int64)
+    p = np.array([0.25, 1 / 255, 2.0 ** -8, 1 / 1024, 1.0])
+    cnt = np.array([1, 1, 1, 1, 1], np.uint32)
+    want = 4 / 4 + 255 / 4 + (256 / 16 + 256 / 256) + (1024 / 16 + 1024 / 256) + 0
+    assert bench.philox_calls(cnt, indeg, p) == pytest.approx(want)
+    cnt = np.array([3, 0, 2, 0, 7], np.uint32)
+    assert bench.philox_calls(cnt, indeg, p) == pytest.approx(3 * 1 + 2 * 17)
+    assert bench.coin_count(cnt, indeg) == 3 * 4 + 2 * 256
+
+
+def test_row_probability_weighted_cascade():
+    g = I.wc_weights(I.er(300, 2000, 3))
+    p = bench.row_probability(g)
+    d = g.indegree()
+    nz = d > 0
+    assert np.array_equal(p[nz].astype(np.float32), (np.float32(1.0) / d[nz].astype(np.float32)))
+    assert np.all(p[~nz] == 1.0)
+
+
+def test_roofline_lines():
+    r = bench.roofline("sample_ic_kernel", coins=8e9, calls=6e8, alg_bytes=1e9, members=5e7, kern_s=0.01,
+                       n_launch=4, philox_calls_per_s=4.9e11, hbm_peak=6644.1, peak_kind="measured",
+                       traffic=1.0e8, large_launches=2)
+    assert r["bound"] == "alu" and r["unit"] == "G Philox calls/s"
+    assert r["achieved"] == pytest.approx(60.0) and r["peak"] == pytest.approx(490.0)
+    assert r["frac"] == pytest.approx(60.0 / 490.0)
+    assert r["calls_per_launch"] == pytest.approx(1.5e8) and r["avg_launch_ms"] == pytest.approx(2.5)
+    lt = bench.roofline("sample_lt_kernel", coins=0, calls=0, alg_bytes=0, members=1e8, kern_s=0.02, n_launch=2,
+                        philox_calls_per_s=4.9e11, hbm_peak=6644.1, peak_kind="measured", traffic=None,
+                        large_launches=1)
+    assert lt["bound"] == "hbm" and lt["unit"] == "GB/s"
+    assert lt["achieved"] == pytest.approx(36.0 * 1e8 / 0.02 / 1e9)
+    sel = bench.select_roofline({"kernel_ms": 5.0, "bytes": 6.6441e9, "calls": 4}, 6644.1, "measured")
+    assert sel["achieved"] == pytest.approx(1328.82) and sel["frac"] == pytest.approx(0.2)
+    assert sel["ms_per_selection"] == pytest.approx(1.25)
+    assert bench.select_roofline({"kernel_ms": 0.0, "bytes": 0.0, "calls": 0}, 6644.1, "measured") is None
+
+
+def test_workloads_and_sweeps_resolve():
+    for name, spec in bench.WORKLOADS.items():
+        assert {"graph", "weights", "model"} <= set(spec), name
+    for sweep, points in bench.SWEEPS.items():
+        for name, over in points:
+            assert name in bench.WORKLOADS, (sweep, name)
+            assert set(over) <= {"k", "eps"}
+    assert bench.WORKLOADS["mrim-ic-wc-rmat22-T5"]["rounds"] == 5
+    assert bench.WORKLOADS["imm-ic-wc-rmat22-fresh"]["fresh_final"] is True
+    assert math.isclose(bench.WORKLOADS["imm-ic-wc-rmat22"]["eps"], 0.1)
