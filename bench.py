@@ -486,26 +486,36 @@ def select_roofline(sel: dict, hbm_peak: float, peak_kind: str):
             "bytes_per_selection": sel["bytes"] / sel["calls"], "traffic": None}
 
 
-def cpu_baseline(graph, budget_s: float = 12.0):
-    """The oracle, as it stands, on a bounded sample of the workload on all host cores."""
-    import oracle as O
-    O.build()
-    th = max(1, O.max_threads())
+def _oracle_sample(O, graph, threads: int, budget_s: float):
+    """RR sets of the workload drawn by the oracle for about budget_s seconds, then the greedy over them."""
     o = O.Oracle(graph)
     T = WORKLOAD.get("rounds", 0)
     if T:
         o.set_rounds(T)
     t0 = time.perf_counter()
-    chunk = 4000 if not T else 500
+    chunk = (4000 if not T else 500) if threads > 1 else (500 if not T else 100)
     while time.perf_counter() - t0 < budget_s:
-        o.sample(O.LT if WORKLOAD["model"] == "LT" else O.IC, WORKLOAD["philox_seed"], chunk, th)
+        o.sample(O.LT if WORKLOAD["model"] == "LT" else O.IC, WORKLOAD["philox_seed"], chunk, threads)
     o.greedy(WORKLOAD["k"])
     dt = time.perf_counter() - t0
     n = o.rr_count
     kind = f"{T}-round {WORKLOAD['model']}" if T else WORKLOAD["model"]
-    return {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle",
-            "sample": f"{n} {kind} RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
-                      f"{dt:.1f} s"}
+    return n, dt, (f"{n} {kind} RR sets of the workload (rr_ids 0..{n - 1}) + greedy k={WORKLOAD['k']} over them; "
+                   f"{dt:.1f} s")
+
+
+def cpu_baseline(graph, budget_s: float = 12.0, single_core_s: float = 0.0):
+    """The oracle, as it stands, on a bounded sample of the workload on all host cores; with
+    single_core_s > 0 also on one core (the experiment setup of Sec. V runs sequential IMM on one core)."""
+    import oracle as O
+    O.build()
+    th = max(1, O.max_threads())
+    n, dt, sample = _oracle_sample(O, graph, th, budget_s)
+    r = {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle", "sample": sample}
+    if single_core_s > 0:
+        n1, dt1, sample1 = _oracle_sample(O, graph, 1, single_core_s)
+        r["single_core"] = {"value": n1 / dt1, "unit": "RR-sets/s", "cores": 1, "sample": sample1}
+    return r
 
 
 def run_reference(args):
@@ -669,7 +679,7 @@ def run_ours(args):
             "clocks": clk.summary(),
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(g, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = cpu_baseline(g, budget_s=args.cpu_budget, single_core_s=args.cpu_single_budget)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -742,6 +752,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--cpu-single-budget", type=float, default=4.0,
+                    help="seconds of one-core oracle work for cpu_baseline.single_core (0: skip)")
     ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=["sample-ic", "sample-lt", "sample-ic-p001", "select"],

@@ -10,6 +10,8 @@
   the selection kernels' time.
 * Every workload name resolves to a graph recipe and every sweep point to a
   workload.
+* The CPU baseline runs the oracle on all host cores and, when asked, on one
+  core, each over a bounded sample it describes.
 """
 import math
 
@@ -69,3 +71,14 @@ def test_workloads_and_sweeps_resolve():
     assert bench.WORKLOADS["mrim-ic-wc-rmat22-T5"]["rounds"] == 5
     assert bench.WORKLOADS["imm-ic-wc-rmat22-fresh"]["fresh_final"] is True
     assert math.isclose(bench.WORKLOADS["imm-ic-wc-rmat22"]["eps"], 0.1)
+
+
+def test_cpu_baseline_all_cores_and_one_core(monkeypatch):
+    g = I.wc_weights(I.er(2000, 20000, 1))
+    monkeypatch.setattr(bench, "WORKLOAD", dict(bench.WORKLOAD, k=10))
+    r = bench.cpu_baseline(g, budget_s=0.05, single_core_s=0.05)
+    assert r["kind"] == "oracle" and r["unit"] == "RR-sets/s" and r["cores"] >= 1 and r["value"] > 0
+    assert int(r["sample"].split()[0]) > 0 and "greedy k=10" in r["sample"]
+    one = r["single_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and int(one["sample"].split()[0]) > 0
+    assert "single_core" not in bench.cpu_baseline(g, budget_s=0.05)
