@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point include/gim.h declares.
+"""The C-ABI library loads and exports exactly the entry points include/gim.h declares.
 
 No compute call is made here, so this runs without a GPU.
 """
@@ -40,6 +40,20 @@ def test_every_declared_symbol_is_exported(lib):
     for name in _declared():
         assert hasattr(lib, name), name
         assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_no_undeclared_exports(lib):
+    """Every gim_* symbol the library exports is declared in include/ (no undocumented entry points)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    from paper_2009_07325_gb300 import binding
+    out = subprocess.run([nm, "-D", "--defined-only", lib._name], capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split()[-1].startswith("gim_") and " T " in ln}
+    assert exported, "no gim_* exports found"
+    assert exported == _declared(), (sorted(exported - _declared()), sorted(_declared() - exported))
 
 
 def test_binding_covers_every_declared_symbol():
