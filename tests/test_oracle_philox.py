@@ -1,8 +1,9 @@
 """Pins of the oracle's Philox4x32-10 and of the coin / root / LT draws built on it.
 
-The oracle's Philox (Salmon et al., SC'11) is checked against an independent
-implementation of the same generator, triton's ``tl.philox`` run on the CPU by
-triton's interpreter, over random counters and keys. The draws that use it
+The oracle's Philox (Salmon et al., SC'11) is checked against the generator's
+published known-answer vectors and against an independent implementation of
+the same generator, triton's ``tl.philox`` run on the CPU by triton's
+interpreter, over random counters and keys. The draws that use it
 are then checked statistically: uniformity of the words, the IC coin rate per
 edge probability, and the uniformity of the root draw.
 """
@@ -67,6 +68,18 @@ def test_philox_matches_triton_interpreter(oracle_mod, tmp_path):
         for ctr, t in zip(case["ctr"], tri):
             o = oracle_mod.philox4x32_10(np.array(ctr, np.uint32), key)
             assert o.tolist() == t, (seed, ctr)
+
+
+def test_philox_known_answers(oracle_mod):
+    """The generator's published known-answer vectors (tests/golden/philox4x32_10_kat.json)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.json")
+    kat = json.load(open(path))
+    assert len(kat["cases"]) == 3
+    for case in kat["cases"]:
+        ctr = np.array([int(x, 16) for x in case["ctr"]], np.uint32)
+        key = np.array([int(x, 16) for x in case["key"]], np.uint32)
+        want = [int(x, 16) for x in case["out"]]
+        assert oracle_mod.philox4x32_10(ctr, key).tolist() == want, case
 
 
 def test_philox_words_uniform(oracle_mod):
