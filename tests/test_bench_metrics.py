@@ -12,6 +12,9 @@
   workload.
 * The CPU baseline runs the oracle on all host cores and, when asked, on one
   core, each over a bounded sample it describes.
+* The served query trace (Poisson arrivals at 50 q/s, k uniform on [10, 200],
+  eps log-uniform on [0.05, 0.5], IC or LT half each) and the batch recipe
+  (n = round(10^(4+2U)), k and eps from fixed sets, seed 1000 + i).
 """
 import math
 
@@ -82,3 +85,38 @@ def test_cpu_baseline_all_cores_and_one_core(monkeypatch):
     one = r["single_core"]
     assert one["cores"] == 1 and one["value"] > 0 and int(one["sample"].split()[0]) > 0
     assert "single_core" not in bench.cpu_baseline(g, budget_s=0.05)
+
+
+def test_serve_trace_distributions():
+    N = 20000
+    tr = bench.serve_trace(N)
+    t = np.array([x[0] for x in tr])
+    gaps = np.diff(np.r_[0.0, t])
+    assert np.all(gaps > 0)
+    rate = 50.0
+    assert abs(gaps.mean() - 1 / rate) < 5 * (1 / rate) / math.sqrt(N)          # Poisson at 50 q/s
+    frac = float(np.mean(gaps > 1 / rate))
+    assert abs(frac - math.exp(-1)) < 5 * math.sqrt(math.exp(-1) * (1 - math.exp(-1)) / N)   # exponential gaps
+    k = np.array([x[1][1] for x in tr])
+    assert k.min() >= 10 and k.max() <= 200
+    cnt = np.bincount(k - 10, minlength=191)
+    chi2 = float(((cnt - N / 191) ** 2 / (N / 191)).sum())
+    assert abs(chi2 - 190) < 6 * math.sqrt(2 * 190)                              # k uniform on [10, 200]
+    eps = np.array([x[1][2] for x in tr])
+    z = np.log10(eps / 0.05)
+    assert z.min() >= 0 and z.max() < 1 and abs(z.mean() - 0.5) < 5 * math.sqrt(1 / 12 / N)   # log-uniform
+    lt = np.mean([x[1][0] == 1 for x in tr])
+    assert abs(lt - 0.5) < 5 * math.sqrt(0.25 / N)
+    assert all(x[1][3] == 1.0 for x in tr)
+    assert bench.serve_trace(60) == tr[:60]
+
+
+def test_batch_instances_recipe():
+    inst = bench.batch_instances(256)
+    assert len(inst) == 256 and inst == bench.batch_instances(256)
+    ns = np.array([x[0] for x in inst])
+    assert ns.min() >= 10 ** 4 and ns.max() <= 10 ** 6
+    z = np.log10(ns) - 4
+    assert abs(z.mean() - 1.0) < 5 * math.sqrt(4 / 12 / 256)                    # n = round(10^(4 + 2U))
+    assert {x[1][1] for x in inst} == {10, 25, 50} and {x[1][2] for x in inst} == {0.1, 0.2, 0.5}
+    assert [x[1][4] for x in inst] == [1000 + i for i in range(256)]
