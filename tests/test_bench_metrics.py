@@ -15,6 +15,8 @@
 * The served query trace (Poisson arrivals at 50 q/s, k uniform on [10, 200],
   eps log-uniform on [0.05, 0.5], IC or LT half each) and the batch recipe
   (n = round(10^(4+2U)), k and eps from fixed sets, seed 1000 + i).
+* The clock record: median SM clock, maximum, and the throttle reasons seen
+  active, parsed from nvidia-smi's CSV samples.
 """
 import math
 
@@ -120,3 +122,25 @@ def test_batch_instances_recipe():
     assert abs(z.mean() - 1.0) < 5 * math.sqrt(4 / 12 / 256)                    # n = round(10^(4 + 2U))
     assert {x[1][1] for x in inst} == {10, 25, 50} and {x[1][2] for x in inst} == {0.1, 0.2, 0.5}
     assert [x[1][4] for x in inst] == [1000 + i for i in range(256)]
+
+
+def test_clock_summary_parses_nvidia_smi_lines(tmp_path):
+    rows = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2040, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped sample
+        "0, 1980, 2070, 1400.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    s = bench.ClockSampler(0)
+    s.path = str(path)
+    out = s.summary()
+    assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    assert not path.exists()                 # the sample file is removed after reading
+    assert s.summary() is None
+    empty = tmp_path / "empty.csv"
+    empty.write_text("")
+    s.path = str(empty)
+    assert s.summary() is None
