@@ -79,3 +79,13 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.gim_create(ctypes.byref(h), 0, None) != 0
     assert not h.value
+
+
+def test_build_covers_every_translation_unit_for_sm_103a():
+    from paper_2009_07325_gb300 import build
+    cus = {f for f in os.listdir(build.CSRC) if f.endswith(".cu")}
+    assert set(build.SOURCES) == cus and len(build.SOURCES) == len(cus)
+    f = build.flags()
+    assert "arch=compute_103a,code=sm_103a" in f and f[f.index("arch=compute_103a,code=sm_103a") - 1] == "-gencode"
+    assert "-lineinfo" in f and not any(x.startswith("-march") for x in f)
+    assert sum(1 for x in f if x == "-gencode") == 1       # one target: GB300 only
