@@ -89,3 +89,11 @@ def test_build_covers_every_translation_unit_for_sm_103a():
     assert "arch=compute_103a,code=sm_103a" in f and f[f.index("arch=compute_103a,code=sm_103a") - 1] == "-gencode"
     assert "-lineinfo" in f and not any(x.startswith("-march") for x in f)
     assert sum(1 for x in f if x == "-gencode") == 1       # one target: GB300 only
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without libgim.so the binding raises instead of computing anything."""
+    from paper_2009_07325_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="libgim.so not found"):
+        binding.load_library(str(tmp_path / "libgim.so"))
