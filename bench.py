@@ -511,7 +511,8 @@ def cpu_baseline(graph, budget_s: float = 12.0, single_core_s: float = 0.0):
     O.build()
     th = max(1, O.max_threads())
     n, dt, sample = _oracle_sample(O, graph, th, budget_s)
-    r = {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle", "sample": sample}
+    r = {"value": n / dt, "unit": "RR-sets/s", "cores": th, "kind": "oracle", "sample": sample,
+         "rr_sets": n, "seconds": dt}
     if single_core_s > 0:
         n1, dt1, sample1 = _oracle_sample(O, graph, 1, single_core_s)
         r["single_core"] = {"value": n1 / dt1, "unit": "RR-sets/s", "cores": 1, "sample": sample1}
@@ -528,8 +529,8 @@ def run_reference(args):
         r = cpu_baseline(g, budget_s=args.ref_budget)
         if i >= args.warmup:
             steps.append(r)
-    units = sum(float(r["sample"].split()[0]) for r in steps)
-    secs = sum(float(r["sample"].split()[0]) / r["value"] for r in steps)
+    units = float(sum(r["rr_sets"] for r in steps))
+    secs = sum(r["seconds"] for r in steps)
     value = units / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RR-sets/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,

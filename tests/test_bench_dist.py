@@ -73,3 +73,39 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     assert bench.run_reference(ns) == 0
     assert called == []
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_rank0_line(monkeypatch, capsys):
+    """Rank 0 times the oracle for warmup + steps bounded samples and prints one line whose value is
+    the timed steps' RR sets over their seconds, with the reference arm's keys."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2009_07325_gb300 import inputs as I
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    g = I.wc_weights(I.er(2000, 20000, 1))
+    monkeypatch.setattr(bench, "load_workload", lambda: g)
+    monkeypatch.setattr(bench, "WORKLOAD", dict(bench.WORKLOAD, k=10))
+    seen = []
+    real = bench.cpu_baseline
+
+    def spy(graph, budget_s):
+        r = real(graph, budget_s=budget_s)
+        seen.append(r)
+        return r
+
+    monkeypatch.setattr(bench, "cpu_baseline", spy)
+    ns = type("A", (), dict(warmup=1, steps=2, ref_budget=0.05))()
+    assert bench.run_reference(ns) == 0
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    assert len(seen) == 3
+    timed = seen[1:]
+    want = sum(r["rr_sets"] for r in timed) / sum(r["seconds"] for r in timed)
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(want)
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "RR-sets/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["ms_per_step"] == pytest.approx(1e3 * sum(r["seconds"] for r in timed) / 2)
