@@ -33,12 +33,15 @@
  *    rr_id t * 2^32 + j with the root of RR set j; elements t * n + v; the
  *    greedy picks k per round; the constants use T ln C(n, k) and the
  *    partition-matroid guarantee 1/2 (Sun et al.'s own rules are not in
- *    the paper: parity unpinned for those constants).
+ *    the paper; that choice of N_S and ratio is a reading).
  *
- * parity unpinned: the exact IMM constants (lambda', lambda*) against
- * Tang et al.'s own code, which the paper does not print. Everything else
- * here is pinned by the CPU tests against exhaustive enumeration, brute
- * force, library routines and invariants.
+ * Pins: everything here is pinned by the CPU tests against exhaustive
+ * enumeration, brute force, library routines and invariants. The IMM
+ * constants (ell', lambda', lambda*) are pinned by the concentration
+ * bounds they are derived from in IMM's analysis: each tail bound, at the
+ * constants' sample sizes, comes out at exactly its failure-probability
+ * target, and the error budget eps is spent exactly; the same conditions
+ * pin the multi-round constants under the reading above.
  */
 #include <math.h>
 #include <stdint.h>
