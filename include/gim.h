@@ -188,9 +188,11 @@ gim_status gim_mrim(gim_ctx *ctx, gim_model model, uint32_t rounds, uint32_t k, 
  * library allocate device memory - processes whose device memory is
  * reserved up front by their own pool or arena, where a foreign cudaMalloc
  * would fail or break their budget, and latency-critical paths that cannot
- * afford the synchronisation an allocation may bring. It computes exactly
- * what gim_select_seeds computes (same kernels, same tie rule), over an RR
- * collection the caller holds in device memory, and needs no context.
+ * afford the synchronisation an allocation may bring. It returns the same
+ * seeds, gains and covered count as gim_select_seeds (same tie rule: lowest
+ * id), over an RR collection the caller holds in device memory, and needs
+ * no context. It runs the k rounds as a per-round pair of kernels (argmax,
+ * then cover), not gim_select_seeds's persistent greedy kernel.
  *   n:             number of vertices, 1 <= n <= 65536.
  *   num_sets:      number of RR sets R, <= 262144.
  *   num_members:   total members Z = d_rr_offsets[R], <= 1048576.
@@ -207,8 +209,10 @@ gim_status gim_mrim(gim_ctx *ctx, gim_model model, uint32_t rounds, uint32_t k, 
  * Scratch: one fixed array of about 6.6 MB in the library's device image,
  * present on every device that loads the library until the process exits.
  * The first call on a device looks up the array's device address (set-up,
- * done once per device under a lock); make that first call before any stream
- * capture begins. Every call on a device shares the array and finds it as
+ * done once per device under a lock) and keeps it for the life of the
+ * process, so that first call should come before any stream capture begins,
+ * and the call must not be used on a device after cudaDeviceReset (the
+ * kept address would be stale). Every call on a device shares the array and finds it as
  * the previous call left it (the call clears what must start at zero), so
  * calls whose work overlaps on the GPU - concurrent streams, or concurrent
  * host threads on one device - race and must be serialised by the caller.

@@ -129,32 +129,10 @@ gim_status ensure_lt(gim_ctx *ctx) {
 // (a failure to build them leaves the error on ctx and reads as not valid).
 bool lt_valid(gim_ctx *ctx) { return ensure_lt(ctx) == GIM_OK && ctx->lt_ok == 1; }
 
-gim_status shared_acquire(gim_ctx *ctx) {
-  DeviceShared &D = g_shared[ctx->device];
-  std::lock_guard<std::mutex> lock(D.mu);
-  if (D.refs == 0) {
-    D.sm_count = ctx->sm_count;
-    const uint32_t workers = (uint32_t)ctx->sm_count * (uint32_t)ic_common_blocks_per_sm() * 8u;
-    D.cs.workers = workers;
-    CU(cudaMalloc(&D.cs.queue, (uint64_t)workers * kQueueCap * 4));
-    CU(cudaMalloc(&D.cs.hash, (uint64_t)workers * kHashSlots * 8));
-    CU(cudaMalloc(&D.cs.epoch, (uint64_t)workers * 4));
-    CU(cudaMemset(D.cs.hash, 0, (uint64_t)workers * kHashSlots * 8));
-    CU(cudaMemset(D.cs.epoch, 0, (uint64_t)workers * 4));
-    CU(cudaMalloc(&D.d_ctl, sizeof(SampleCtl)));
-    CU(cudaMalloc(&D.lt_ovf, (uint64_t)kLtOvfSlots * kLtGroupPath * sizeof(uint32_t)));
-    CU(cudaMalloc(&D.d_ovf_next, sizeof(unsigned int)));
-    CU(cudaMallocHost(&D.h_ctl, sizeof(SampleCtl)));
-    D.lt_grid = (uint32_t)ctx->sm_count * (uint32_t)lt_common_blocks_per_sm();
-  }
-  D.refs++;
-  return GIM_OK;
-}
+namespace {
 
-void shared_release(int device) {
-  DeviceShared &D = g_shared[device];
-  std::lock_guard<std::mutex> lock(D.mu);
-  if (--D.refs > 0) return;
+// Frees every buffer of D (the caller holds D.mu).
+void shared_free(DeviceShared &D) {
   dfree(D.cs.queue);
   dfree(D.cs.hash);
   dfree(D.cs.epoch);
@@ -176,6 +154,41 @@ void shared_release(int device) {
   if (D.h_ctl) cudaFreeHost(D.h_ctl);
   D.h_ctl = nullptr;
   D.refs = 0;
+}
+
+}  // namespace
+
+gim_status shared_acquire(gim_ctx *ctx) {
+  DeviceShared &D = g_shared[ctx->device];
+  std::lock_guard<std::mutex> lock(D.mu);
+  if (D.refs == 0) {
+    D.sm_count = ctx->sm_count;
+    const uint32_t workers = (uint32_t)ctx->sm_count * (uint32_t)ic_common_blocks_per_sm() * 8u;
+    D.cs.workers = workers;
+    cudaError_t e = cudaMalloc(&D.cs.queue, (uint64_t)workers * kQueueCap * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&D.cs.hash, (uint64_t)workers * kHashSlots * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&D.cs.epoch, (uint64_t)workers * 4);
+    if (e == cudaSuccess) e = cudaMemset(D.cs.hash, 0, (uint64_t)workers * kHashSlots * 8);
+    if (e == cudaSuccess) e = cudaMemset(D.cs.epoch, 0, (uint64_t)workers * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&D.d_ctl, sizeof(SampleCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&D.lt_ovf, (uint64_t)kLtOvfSlots * kLtGroupPath * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&D.d_ovf_next, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMallocHost(&D.h_ctl, sizeof(SampleCtl));
+    if (e != cudaSuccess) {
+      shared_free(D);   // nothing is kept from a failed set-up, so a retry starts clean
+      return cuda_err(ctx, e, "per-device sampling scratch");
+    }
+    D.lt_grid = (uint32_t)ctx->sm_count * (uint32_t)lt_common_blocks_per_sm();
+  }
+  D.refs++;
+  return GIM_OK;
+}
+
+void shared_release(int device) {
+  DeviceShared &D = g_shared[device];
+  std::lock_guard<std::mutex> lock(D.mu);
+  if (--D.refs > 0) return;
+  shared_free(D);
 }
 
 namespace {

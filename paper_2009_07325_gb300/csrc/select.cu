@@ -293,10 +293,11 @@ cudaError_t ensure(T *&p, uint64_t &cap, uint64_t need) {
 // device memory is fully reserved up front by their own pool or arena (so a
 // foreign allocation would fail or break their budget), and latency-critical
 // paths that cannot afford the synchronisation an allocation may imply. For
-// them this entry point runs the same selection kernels as gim_select_seeds
-// with every scratch buffer carved out of one fixed-size array that lives in
-// the library's device image. Callers pass their inputs and outputs in device
-// memory they own.
+// them this entry point returns what gim_select_seeds returns (the same
+// seeds, gains and covered count), running the k rounds as argmax_kernel /
+// cover_kernel pairs, with every scratch buffer carved out of one fixed-size
+// array that lives in the library's device image. Callers pass their inputs
+// and outputs in device memory they own.
 // ===========================================================================
 namespace {
 
