@@ -1,0 +1,189 @@
+"""GPU parity with the oracle on the workloads at their stated sizes.
+
+* R-MAT scale 20 (seed 2), IC weighted cascade, k = 50, eps = 0.1: one full
+  IMM (Alg. 2, Alg. 1); a seeded sample of its RR sets and the largest ones
+  redrawn by the oracle one by one, the occurrence counts against the
+  exported store, and the oracle's IMM replayed over the GPU's collection
+  (same seeds, theta, LB and |R|).
+* The 256-instance Chung-Lu batch (the benchmark's instances: n log-uniform
+  in [10^4, 10^6], k from {10, 25, 50}, eps from {0.1, 0.2, 0.5}, one
+  persistent launch per round, autotuned schedule): every instance equals
+  its lone gim_imm, and the oracle's IMM, drawn from scratch on the host,
+  equals the batch on the largest and the smallest instance of every
+  (k, eps) pair.
+* The R-MAT scale 24 server (the benchmark's trace: 60 Poisson arrivals at
+  50 queries/s, k uniform in [10, 200], eps log-uniform in [0.05, 0.5],
+  IC / LT half each, 8 slots): every result equals a lone gim_imm, and the
+  two IC and two LT queries with the fewest RR sets are replayed by the
+  oracle over the prefix of the pool they used (the first |R| RR sets of
+  their model and seed, sampled again through gim_sample_rr, spot-checked
+  against the oracle).
+* R-MAT scale 22 under IC with uniform p = 0.01, k = 100, eps = 0.2 (the
+  eps the benchmark runs this graph at): the collections of the first two
+  rounds of the lower-bound search (theta_1 = 64,575 and theta_2 = 129,149
+  sets, about 10^4 members per set on average, 2.5 and 5 GB) exported and
+  selected over by the oracle's greedy: same seeds, gains and covered count.
+  (At eps = 0.05 the first round alone is 966,428 sets, about 37 GB.)
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import bench
+import oracle as O
+from paper_2009_07325_gb300 import GIM_IC, GIM_LT, Context, binding
+from paper_2009_07325_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, O.max_threads())
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2009_07325_gb300 import build
+    build.build()
+    O.build()
+    I.build()
+
+
+def _sampled_sets_match(orc, model, seed, off, mem, n_sample=256, rng_seed=12345):
+    R = len(off) - 1
+    rng = np.random.default_rng(rng_seed)
+    sizes = np.diff(off)
+    ids = set(rng.choice(R, size=min(n_sample, R), replace=False).tolist())
+    ids |= set(np.argsort(sizes)[-8:].tolist()) | {0, R - 1}
+    for j in sorted(ids):
+        got = np.sort(mem[off[j]:off[j + 1]])
+        want = np.sort(orc.rr_one(model, seed, int(j)))
+        assert np.array_equal(got, want), f"RR set {j} differs"
+
+
+def test_imm_rmat20_ic_wc_full_size():
+    g = I.wc_weights(I.rmat(20, 2))
+    k, eps = 50, 0.1
+    ctx = Context(0)
+    ctx.load(g)
+    binding.autotune([ctx], [(GIM_IC, k, eps, 1.0, 7)], 20000)
+    r = ctx.imm(GIM_IC, k, eps, 1.0, 7)
+    off, mem = ctx.rr_export()
+    assert len(off) - 1 == r["rr_count"] >= r["theta"]
+    assert np.array_equal(ctx.coverage(), np.bincount(mem, minlength=g.n).astype(np.uint32))
+    orc = O.Oracle(g)
+    _sampled_sets_match(orc, GIM_IC, 7, off, mem)
+    orc.load_csr(off, mem)
+    o = orc.imm_replay(k, eps, 1.0)
+    assert r["seeds"].tolist() == o["seeds"].tolist()
+    assert (r["theta"], r["lb"], r["rr_count"]) == (o["theta"], o["lb"], o["rr_count"])
+    # the greedy's gains and covered count on the final collection as well
+    orc.load_csr(off, mem)
+    s, gains, cov = ctx.select_seeds(k)
+    os_, og, oc = orc.greedy(k)
+    assert (s.tolist(), gains.tolist(), cov) == (os_.tolist(), og.tolist(), oc)
+    ctx.close()
+
+
+def test_batch_256_chunglu_matches_lone_runs_and_oracle():
+    specs = bench.batch_instances(256)
+    graphs = [I.wc_weights(I.chung_lu(n, 1000 + i)) for i, (n, _) in enumerate(specs)]
+    params = [p for _, p in specs]
+    ctxs = []
+    for g in graphs:
+        c = Context(0)
+        c.load(g)
+        ctxs.append(c)
+    binding.autotune(ctxs, params, 2000)
+    res = binding.batch_imm(ctxs, params)
+    # the oracle on the largest and the smallest instance of every (k, eps) pair
+    pick = {}
+    for i, (n, p) in enumerate(specs):
+        key = (p[1], p[2])
+        lo, hi = pick.get(key, (i, i))
+        if n < specs[lo][0]:
+            lo = i
+        if n > specs[hi][0]:
+            hi = i
+        pick[key] = (lo, hi)
+    checked = sorted({i for lo_hi in pick.values() for i in lo_hi})
+    assert len(pick) == 9 and len(checked) >= 9
+    for i in checked:
+        p = params[i]
+        o = O.Oracle(graphs[i]).imm(p[0], p[1], p[2], p[3], p[4], THREADS)
+        r = res[i]
+        assert r["seeds"].tolist() == o["seeds"].tolist(), (i, p)
+        assert (r["theta"], r["lb"], r["rr_count"]) == (o["theta"], o["lb"], o["rr_count"]), (i, p)
+        assert r["lb_rounds"] == len(o["rounds"]), (i, p)
+    # every instance equals its lone run
+    for i, (c, p) in enumerate(zip(ctxs, params)):
+        a = c.imm(*p)
+        assert res[i]["seeds"].tolist() == a["seeds"].tolist(), (i, p)
+        assert (res[i]["theta"], res[i]["lb"], res[i]["rr_count"]) == (a["theta"], a["lb"], a["rr_count"]), (i, p)
+    for c in ctxs:
+        c.close()
+
+
+def test_server_rmat24_trace_matches_lone_runs_and_oracle():
+    g = I.wc_weights(I.rmat(24, 4))
+    ctx = Context(0)
+    ctx.load(g)
+    trace = bench.serve_trace(60)
+    srv = binding.Server(ctx, max_active=bench.SERVE_SLOTS, max_k=200)
+    tickets = []
+    start = time.perf_counter()
+    for arr, p in trace:                       # arrivals in real time: later queries join running ones
+        d = start + arr - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(srv.submit(*p))
+    got = [srv.wait(t, 1800) for t in tickets]
+    st = srv.stats()
+    srv.stop()
+    assert st["completed"] == len(trace) and st["peak_active"] > 1
+    for (_, p), r in zip(trace, got):
+        a = ctx.imm(*p)
+        assert r["seeds"].tolist() == a["seeds"].tolist(), p
+        assert (r["theta"], r["lb"], r["rr_count"]) == (a["theta"], a["lb"], a["rr_count"]), p
+    # the oracle over the pool prefix of the two IC and two LT queries with the fewest sets
+    orc = O.Oracle(g)
+    for model in (GIM_IC, GIM_LT):
+        idx = sorted((r["rr_count"], i) for i, ((_, p), r) in enumerate(zip(trace, got)) if p[0] == model)[:2]
+        for _, i in idx:
+            p, r = trace[i][1], got[i]
+            pool = Context(0)
+            pool.load(g)
+            pool.sample_rr(model, r["rr_count"], p[4])
+            off, mem = pool.rr_export()
+            pool.close()
+            _sampled_sets_match(orc, model, p[4], off, mem, n_sample=48, rng_seed=i)
+            orc.load_csr(off, mem)
+            o = orc.imm_replay(p[1], p[2], p[3])
+            assert r["seeds"].tolist() == o["seeds"].tolist(), p
+            assert (r["theta"], r["lb"], r["rr_count"]) == (o["theta"], o["lb"], o["rr_count"]), p
+    ctx.close()
+
+
+def test_ic_p001_rmat22_lower_bound_collections_oracle_greedy():
+    g = I.uniform_weights(I.rmat(22, 3), 0.01)
+    k, eps = 100, 0.2
+    c = O.imm_constants(g.n, k, eps, 1.0)
+    ctx = Context(0)
+    ctx.load(g)
+    orc = O.Oracle(g)
+    have = 0
+    for i in (1, 2):
+        theta_i = math.ceil(c["lambda_prime"] / (g.n / 2 ** i))
+        ctx.sample_rr(GIM_IC, theta_i - have, 7)
+        have = theta_i
+        s, gains, cov = ctx.select_seeds(k)
+        off, mem = ctx.rr_export()
+        assert len(off) - 1 == theta_i
+        assert np.array_equal(ctx.coverage(), np.bincount(mem, minlength=g.n).astype(np.uint32))
+        _sampled_sets_match(orc, GIM_IC, 7, off, mem, n_sample=24, rng_seed=i)
+        orc.load_csr(off, mem)
+        del off, mem
+        os_, og, oc = orc.greedy(k)
+        assert s.tolist() == os_.tolist(), i
+        assert gains.tolist() == og.tolist() and cov == oc, i
+        orc.reset()
+    ctx.close()
