@@ -96,8 +96,11 @@ WORKLOADS["serve-rmat24"] = dict(
     arrivals="Poisson, 50 queries/s", queries=60)
 
 
-def serve_trace(count, rate=50.0, seed=5):
-    """Arrival times (s) and query parameters of the serving workload."""
+def serve_trace(count, rate=50.0, seed=5, distinct=False):
+    """Arrival times (s) and query parameters of the serving workload. Every
+    query draws its RR sets with the workload's Philox seed, so queries of one
+    model share them; distinct=True gives query i the Philox seed 2000 + i
+    instead, so no two queries share an RR set."""
     from paper_2009_07325_gb300 import GIM_IC, GIM_LT
     from paper_2009_07325_gb300 import inputs as I
     r = I.u64_stream(seed, 950, 4 * count)
@@ -108,7 +111,7 @@ def serve_trace(count, rate=50.0, seed=5):
         k = 10 + int(u[4 * i + 1] * 191)
         eps = float(0.05 * 10.0 ** u[4 * i + 2])
         model = GIM_IC if u[4 * i + 3] < 0.5 else GIM_LT
-        out.append((t, (model, k, eps, 1.0, WORKLOAD["philox_seed"])))
+        out.append((t, (model, k, eps, 1.0, 2000 + i if distinct else WORKLOAD["philox_seed"])))
     return out
 
 
@@ -175,8 +178,24 @@ def run_serve(args):
     srv.stop()
     plain(warm[:2])
     p_res, p_lat, p_span = plain(trace)
-    same = all(a["seeds"].tolist() == b["seeds"].tolist() and a["theta"] == b["theta"] for a, b in zip(s_res, p_res))
-    same_c = all(a["seeds"].tolist() == b["seeds"].tolist() and a["theta"] == b["theta"] for a, b in zip(c_res, p_res))
+    same_res = lambda xs, ys: all(a["seeds"].tolist() == b["seeds"].tolist() and a["theta"] == b["theta"]
+                                  for a, b in zip(xs, ys))
+    same = same_res(s_res, p_res)
+    same_c = same_res(c_res, p_res)
+    # distinct Philox seeds: no query shares an RR set with another, so the
+    # served speed-up is the overlap of continuous batching alone; against
+    # one query at a time through gim_imm and through a one-slot server
+    dtrace = serve_trace(WORKLOAD["queries"], distinct=True)
+    srv = binding.Server(ctx, max_active=SERVE_SLOTS, max_k=200)
+    with ClockSampler(local) as dclk:
+        d_res, d_lat, d_span = served(srv, dtrace)
+    d_st = srv.stats()
+    srv.stop()
+    srv = binding.Server(ctx, max_active=1, max_k=200)
+    o_res, o_lat, o_span = served(srv, dtrace)
+    srv.stop()
+    dp_res, dp_lat, dp_span = plain(dtrace)
+    same_d = same_res(d_res, dp_res) and same_res(o_res, dp_res)
     q = len(trace)
     pct = lambda x, p: float(np.percentile(np.array(x), p))
     line = {"metric": "served IMM queries/s with p50/p99 latency (R-MAT-24, Poisson 50 q/s, IC/LT mix)",
@@ -194,6 +213,21 @@ def run_serve(args):
             "plain_one_at_a_time": {"queries_per_s": q / p_span, "p50_ms": pct(p_lat, 50), "p99_ms": pct(p_lat, 99),
                                     "makespan_s": p_span},
             "throughput_vs_plain": (q / s_span) / (q / p_span),
+            "shared_seed_note": "every query above uses Philox seed 7, so queries of one model share RR sets "
+                                "(resident pools); distinct_seeds below shares none",
+            "distinct_seeds": {
+                "philox_seeds": "2000 + query index", "queries": len(dtrace),
+                "served": {"queries_per_s": q / d_span, "p50_ms": pct(d_lat, 50), "p99_ms": pct(d_lat, 99),
+                           "makespan_s": d_span, "pools": "empty at start (fresh server)",
+                           "rounds": d_st["rounds"], "peak_active": d_st["peak_active"],
+                           "sample_ms": d_st["sample_ms"], "select_ms": d_st["select_ms"]},
+                "one_slot_server": {"queries_per_s": q / o_span, "p50_ms": pct(o_lat, 50),
+                                    "p99_ms": pct(o_lat, 99), "makespan_s": o_span},
+                "plain_one_at_a_time": {"queries_per_s": q / dp_span, "p50_ms": pct(dp_lat, 50),
+                                        "p99_ms": pct(dp_lat, 99), "makespan_s": dp_span},
+                "throughput_vs_plain": (q / d_span) / (q / dp_span),
+                "throughput_vs_one_slot": (q / d_span) / (q / o_span),
+                "identical_seed_sets": bool(same_d), "clocks": dclk.summary()},
             "identical_seed_sets": bool(same and same_c), "graph_generation_s": t_gen, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -201,17 +235,17 @@ def run_serve(args):
     return 0
 
 
-def run_batch(args):
-    """Batched IMM (gim_batch_imm over all instances) against the same
-    instances run one after another with gim_imm, graphs resident."""
+def batch_measure(local, steps, warmup, count=256):
+    """Batched IMM (gim_batch_imm over the instances of the batch workload)
+    against the same instances run one after another with gim_imm, graphs
+    resident: batch seconds (median of `steps` timed batches), plain seconds,
+    identical seed sets, and the split of the time."""
     import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2009_07325_gb300 import Context, binding
     from paper_2009_07325_gb300 import inputs as I
-    specs = batch_instances(WORKLOAD["instances"])
+    specs = batch_instances(count)
     t0 = time.perf_counter()
     graphs = [I.wc_weights(I.chung_lu(n, 1000 + i)) for i, (n, _) in enumerate(specs)]
     t_gen = time.perf_counter() - t0
@@ -221,16 +255,17 @@ def run_batch(args):
         c = Context(local, stream=stream.cuda_stream)
         c.load(g)
         ctxs.append(c)
+    del graphs
     params = [p for _, p in specs]
     batch_budget, _ = binding.autotune(ctxs, params, 2000)        # schedule for the batch as a whole
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         res = binding.batch_imm(ctxs, params)
     ctxs[0].reset_timings()
     launches0 = ctxs[0].launch_count()
     torch.cuda.synchronize()
     bt = []
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             t1 = time.perf_counter()
             res = binding.batch_imm(ctxs, params)
             torch.cuda.synchronize()
@@ -255,30 +290,44 @@ def run_batch(args):
         p_select += tp["select_ms"]
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t1
-    same = all(a == b["seeds"].tolist() for a, b in zip(batched_seeds, plain))
+    same = all(a == b["seeds"].tolist() and r["theta"] == b["theta"]
+               for a, r, b in zip(batched_seeds, res, plain))
     t_b = float(np.median(bt))
-    units, secs = aggregate(float(len(ctxs)) * args.steps, sum(bt))
+    out = {"instances": len(ctxs), "batched_s": t_b, "batch_times_s": bt, "plain_sequential_s": t_plain,
+           "speedup_vs_plain": t_plain / t_b, "instances_per_s": len(ctxs) / t_b,
+           "plain_instances_per_s": len(ctxs) / t_plain, "identical_seed_sets": same,
+           "rr_sets": sum(r["rr_count"] for r in res),
+           "batched_split_ms": {"sample": tb["sample_ms"], "select": tb["select_ms"], "wall": tb["wall_ms"]},
+           "plain_split_ms": {"sample": p_sample, "select": p_select,
+                              "common_kernel": sum(c.timings()["kernel_ms"] for c in ctxs),
+                              "large_kernel": sum(c.timings()["large_ms"] for c in ctxs)},
+           "batched_kernel_ms_per_batch": {"common": tb["kernel_ms"] / max(1, steps),
+                                           "large": tb["large_ms"] / max(1, steps)},
+           "rounds": max(r["lb_rounds"] for r in res) + 1,
+           "tuning": {"batch_group_budget": batch_budget,
+                      "plain_group_budgets": sorted(set(plain_budgets)), "by": "gim_autotune"},
+           "gpu_launches": launches, "graph_generation_s": t_gen, "clocks": clk.summary()}
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def run_batch(args):
+    """The batched workload on its own line (see batch_measure)."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    b = batch_measure(local, args.steps, args.warmup, WORKLOAD["instances"])
+    units, secs = aggregate(float(b["instances"]) * args.steps, sum(b["batch_times_s"]))
     line = {"metric": "batched IMM queries/s (256 Chung-Lu instances, IC-WC)", "value": units / secs,
             "unit": "IMM-instances/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": dict(WORKLOAD),
-            "batched_s": t_b, "plain_sequential_s": t_plain, "speedup_vs_plain": t_plain / t_b,
-            "identical_seed_sets": same, "rr_sets": sum(r["rr_count"] for r in res),
-            "batched_split_ms": {"sample": tb["sample_ms"], "select": tb["select_ms"], "wall": tb["wall_ms"]},
-            "plain_split_ms": {"sample": p_sample, "select": p_select,
-                               "common_kernel": sum(c.timings()["kernel_ms"] for c in ctxs),
-                               "large_kernel": sum(c.timings()["large_ms"] for c in ctxs)},
-            "batched_kernel_ms_per_batch": {"common": tb["kernel_ms"] / args.steps,
-                                            "large": tb["large_ms"] / args.steps},
-            "rounds": max(r["lb_rounds"] for r in res) + 1,
-            "tuning": {"batch_group_budget": batch_budget,
-                       "plain_group_budgets": sorted(set(plain_budgets)), "by": "gim_autotune"},
-            "gpu_launches": launches, "graph_generation_s": t_gen, "clocks": clk.summary()}
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": dict(WORKLOAD), **b}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for c in ctxs:
-        c.close()
     return 0
+
+
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -681,8 +730,14 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, budget_s=args.cpu_budget, single_core_s=args.cpu_single_budget)
-        print(json.dumps(line), flush=True)
     ctx.close()
+    if rank == 0:
+        if world == 1 and not args.no_batch and WORKLOAD["workload"] == "imm-ic-wc-rmat22" \
+                and "sweep" not in WORKLOAD:
+            # the batched workload (256 Chung-Lu IMM instances in lockstep against
+            # 256 sequential gim_imm runs), one timed batch after one warm-up
+            line["batch"] = dict(workload="batch-chunglu-256", **batch_measure(local, 1, 1))
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -757,6 +812,8 @@ def main():
                     help="seconds of one-core oracle work for cpu_baseline.single_core (0: skip)")
     ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched-workload object out of the headline line")
     ap.add_argument("--case", default=None, choices=["sample-ic", "sample-lt", "sample-ic-p001", "select"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--count", type=int, default=20000, help="RR sets for --case")

@@ -37,7 +37,7 @@ struct SelDesc {
   uint32_t n, k, active, count_own;       // count_own: cnt is computed here from sets [0, R)
   unsigned long long R;
   unsigned long long fill_R;              // sets this instance adds to the index (0 when ext)
-  unsigned long long set_begin;           // prefix of fill_R over the batch (fill kernel)
+  unsigned long long grp_begin;           // prefix of ceil(fill_R / 32) over the batch (fill kernel)
   unsigned long long count_from;          // count_own: sets [0, count_from) are already in cnt
   unsigned long long cnt_begin;           // prefix of the sets counted this round (count kernel)
   const uint32_t *members;
@@ -65,6 +65,11 @@ struct SelDesc {
   uint64_t *tile_sum;                     // tiles
   unsigned int *bar;                      // greedy group barrier
   uint32_t tile_begin, tiles;             // scan blocks of this instance
+  // 1: the first greedy pick is taken from the occurrence counts before the
+  // index exists (best[0], from bsel_tile_sums); the sets holding it are
+  // marked covered by the fill and left out of the index, and the light
+  // counts are the lengths of the lists filled (bsel_first_*)
+  uint32_t fuse;
 };
 
 // Instance of block b: the last i with begin(i) <= b.
@@ -162,21 +167,42 @@ __global__ void __launch_bounds__(kSelThreads) bsel_count(const SelDesc *d, uint
   }
 }
 
-// Per-tile sums of the occurrence counts.
+// Per-tile sums of the occurrence counts. A tile is kTile consecutive
+// vertices read as kTileItems rows of kSelThreads (coalesced).
 __global__ void __launch_bounds__(kSelThreads) bsel_tile_sums(const SelDesc *d, uint32_t ni) {
   const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
   const SelDesc &D = d[i];
   if (!D.active || D.ext) return;
-  const uint64_t base = (uint64_t)(blockIdx.x - D.tile_begin) * kTile + (uint64_t)threadIdx.x * kTileItems;
-  unsigned long long s = 0;
-  for (uint32_t t = 0; t < kTileItems; ++t)
-    if (base + t < D.n) {
-      const uint32_t c = D.cnt[base + t];
+  const uint64_t base = (uint64_t)(blockIdx.x - D.tile_begin) * kTile + threadIdx.x;
+  unsigned long long s = 0, key = 0;
+#pragma unroll 4
+  for (uint32_t t = 0; t < kTileItems; ++t) {
+    const uint64_t x = base + (uint64_t)t * kSelThreads;
+    if (x < D.n) {
+      const uint32_t c = D.cnt[x];
       s += c < D.hub_min ? c : 0u;        // hubs have no inverted list
+      // the greedy's key (count + 1) << 32 | ~id: the largest is the first pick (lowest id on ties)
+      const unsigned long long kx = ((unsigned long long)(c + 1u) << 32) | (uint32_t)~(uint32_t)x;
+      key = kx > key ? kx : key;
     }
+  }
   unsigned long long ex;
   const unsigned long long tot = block_excl(s, &ex);
   if (threadIdx.x == 0) D.tile_sum[blockIdx.x - D.tile_begin] = tot;
+  if (D.fuse) {   // one atomic per block
+    __shared__ unsigned long long wk[kSelThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(kFullMask, key, o);
+      key = y > key ? y : key;
+    }
+    if ((threadIdx.x & 31u) == 0) wk[threadIdx.x >> 5] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kSelThreads / 32; ++w) key = wk[w] > key ? wk[w] : key;
+      atomicMax(D.best, key);
+    }
+  }
 }
 
 // Exclusive scan of each instance's tile sums (one block per instance).
@@ -199,35 +225,34 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_scan(const SelDesc *d, 
 // Splits the vertices: a hub (count >= hub_min) takes the next hub slot,
 // with its id and count + 1 in hmeta; a light vertex keeps count + 1 in
 // cnt_work and gets its inverted list's offset (exclusive scan of the light
-// counts) and a cursor at that offset.
+// counts) and a cursor at that offset. The tile is scanned row by row
+// (kSelThreads consecutive vertices per row), so every access is coalesced.
 __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint32_t ni) {
   const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
   const SelDesc &D = d[i];
   if (!D.active || D.ext) return;
   const uint32_t tile = blockIdx.x - D.tile_begin;
-  const uint64_t base = (uint64_t)tile * kTile + (uint64_t)threadIdx.x * kTileItems;
-  uint32_t v[kTileItems];
-  unsigned long long s = 0;
-  for (uint32_t t = 0; t < kTileItems; ++t) {
-    v[t] = base + t < D.n ? D.cnt[base + t] : 0u;
-    s += v[t] < D.hub_min ? v[t] : 0u;
-  }
-  unsigned long long ex;
-  block_excl(s, &ex);
-  unsigned long long run = D.tile_sum[tile] + ex;
-  for (uint32_t t = 0; t < kTileItems; ++t) {
-    const uint64_t x = base + t;
-    const bool hub = v[t] >= D.hub_min;
+  unsigned long long run = D.tile_sum[tile];
+  for (uint32_t r = 0; r < kTileItems; ++r) {
+    const uint64_t row0 = (uint64_t)tile * kTile + (uint64_t)r * kSelThreads;
+    if (row0 >= D.n) break;                  // block-uniform
+    const uint64_t x = row0 + threadIdx.x;
+    const uint32_t v = x < D.n ? D.cnt[x] : 0u;
+    const bool hub = v >= D.hub_min;
+    const uint32_t light = hub ? 0u : v;
+    unsigned long long ex;
+    const unsigned long long tot = block_excl(light, &ex);
+    const unsigned long long pos = run + ex;
     if (x < D.n) {
-      D.inv_off[x] = run;
-      D.cursor[x] = run;
+      D.inv_off[x] = pos;
+      D.cursor[x] = pos;
       uint8_t hs = 0xFFu;
-      uint32_t cw = v[t] + 1u;
+      uint32_t cw = v + 1u;
       if (hub) {
         const uint32_t slot = atomicAdd(D.hmeta, 1u);
         if (slot < kHeavyCap) {
           D.hmeta[1 + slot] = (uint32_t)x;
-          D.hmeta[1 + kHeavyCap + slot] = v[t] + 1u;
+          D.hmeta[1 + kHeavyCap + slot] = D.fuse ? 1u : v + 1u;
           hs = (uint8_t)slot;
         } else {
           atomicOr(D.err, 2u);
@@ -236,9 +261,9 @@ __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint
       }
       D.hslot[x] = hs;
       D.cnt_work[x] = cw;
+      if (x + 1 == D.n) D.inv_off[D.n] = pos + light;
     }
-    run += hub ? 0u : v[t];
-    if (x + 1 == D.n) D.inv_off[D.n] = run;
+    run += tot;
   }
 }
 
@@ -276,30 +301,82 @@ __global__ void __launch_bounds__(kSelThreads) bsel_hub_clear(const SelDesc *d, 
   }
 }
 
+// Finds, for a position p of the concatenated member lists of a warp's 32
+// sets, the set that holds it: the last lane s with pre(s) <= p (pre: the
+// exclusive prefix of the set sizes, one per lane; warp-wide).
+__device__ __forceinline__ uint32_t set_of(uint32_t pre, uint32_t p) {
+  uint32_t s = 0;
+#pragma unroll
+  for (uint32_t step = 16; step; step >>= 1) {
+    const uint32_t t = s + step;
+    if (__shfl_sync(kFullMask, pre, t) <= p) s = t;
+  }
+  return s;
+}
+
 // For every set j of every instance: j is appended to the inverted list of
-// each light member and set in the bitmap row of each hub member (one warp
-// per set).
+// each light member and set in the bitmap row of each hub member. A warp
+// takes 32 consecutive sets at a time and walks their members as one list
+// (lane s holds set j0 + s), so small sets fill the lanes; four members per
+// lane are in flight, since the cursor atomics return a value and the loop
+// is bound by their latency. With the fused first pick, a first pass finds
+// the sets that hold the pick: they are marked covered (round 0 covers
+// them), counted for the statistics, and left out of the index.
 __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint32_t ni) {
-  const unsigned long long total = d[ni - 1].set_begin + d[ni - 1].fill_R;   // this round's sets over the batch
+  const unsigned long long total = d[ni - 1].grp_begin + (d[ni - 1].fill_R + 31) / 32;   // groups over the batch
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t g = warp; g < total; g += nwarps) {
-    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.set_begin; });
+    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.grp_begin; });
     const SelDesc &D = d[i];
-    const uint64_t j = g - D.set_begin;
-    const uint64_t b = D.rr_start[j];
-    const uint32_t len = D.rr_len[j];
+    const uint64_t j0 = (g - D.grp_begin) * 32;
+    const uint64_t jl = j0 + lane;
+    const bool valid = jl < D.fill_R;
+    const uint64_t b = valid ? D.rr_start[jl] : 0ull;
+    const uint32_t len = valid ? D.rr_len[jl] : 0u;
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t T = __shfl_sync(kFullMask, incl, 31);   // members of the 32 sets
+    const uint32_t pre = incl - len;
     const bool hubs = D.hmeta[0] != 0u;
-    // four members per lane in flight: the cursor atomics return a value, so
-    // the loop is bound by their latency
-    for (uint32_t t0 = 0; t0 < len; t0 += 128) {
-      uint32_t x[4], hs[4];
+    uint32_t skip = 0;   // bit s: set j0 + s is covered by the first pick
+    if (D.fuse) {
+      const uint32_t u1 = ~(uint32_t)*D.best;
+      uint32_t hit = 0;
+      for (uint32_t p0 = 0; p0 < T; p0 += 128) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t p = p0 + 32 * q + lane;
+          const uint32_t s = set_of(pre, p);
+          const uint64_t bs = ((uint64_t)__shfl_sync(kFullMask, (uint32_t)(b >> 32), s) << 32) |
+                              __shfl_sync(kFullMask, (uint32_t)b, s);
+          const uint32_t ps = __shfl_sync(kFullMask, pre, s);
+          if (p < T && D.members[bs + (p - ps)] == u1) hit |= 1u << s;
+        }
+      }
+      skip = __reduce_or_sync(kFullMask, hit);
+      if ((skip >> lane) & 1u) {
+        atomicOr(D.covered + (jl >> 5), 1u << (jl & 31u));
+        atomicAdd(D.stats, (unsigned long long)len);
+      }
+    }
+    for (uint32_t p0 = 0; p0 < T; p0 += 128) {
+      uint32_t x[4], hs[4], jq[4];
       unsigned long long pos[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const uint32_t t = t0 + 32 * q + lane;
-        x[q] = t < len ? D.members[b + t] : 0xFFFFFFFFu;
+        const uint32_t p = p0 + 32 * q + lane;
+        const uint32_t s = set_of(pre, p);
+        const uint64_t bs = ((uint64_t)__shfl_sync(kFullMask, (uint32_t)(b >> 32), s) << 32) |
+                            __shfl_sync(kFullMask, (uint32_t)b, s);
+        const uint32_t ps = __shfl_sync(kFullMask, pre, s);
+        jq[q] = (uint32_t)j0 + s;
+        x[q] = (p < T && !((skip >> s) & 1u)) ? D.members[bs + (p - ps)] : 0xFFFFFFFFu;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) hs[q] = (hubs && x[q] != 0xFFFFFFFFu) ? D.hslot[x[q]] : 0xFFu;
@@ -307,13 +384,62 @@ __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint3
       for (int q = 0; q < 4; ++q) {
         if (x[q] == 0xFFFFFFFFu) continue;
         if (hs[q] != 0xFFu)
-          atomicOr(D.hbits + (uint64_t)hs[q] * D.words + (j >> 5), 1u << (j & 31u));
+          atomicOr(D.hbits + (uint64_t)hs[q] * D.words + (jq[q] >> 5), 1u << (jq[q] & 31u));
         else
           pos[q] = atomicAdd(&D.cursor[x[q]], 1ull);   // the entry's place in inv, in one round trip
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (x[q] != 0xFFFFFFFFu && hs[q] == 0xFFu) D.inv[pos[q]] = (uint32_t)j;
+        if (x[q] != 0xFFFFFFFFu && hs[q] == 0xFFu) D.inv[pos[q]] = jq[q];
+    }
+  }
+}
+
+// Fused first pick, light side (one block per tile, like bsel_apply): a
+// light vertex's count is the length of its filled list (the uncovered sets
+// holding it), plus one while unselected; the first pick's is 0.
+__global__ void __launch_bounds__(kSelThreads) bsel_first_light(const SelDesc *d, uint32_t ni) {
+  const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
+  const SelDesc &D = d[i];
+  if (!D.active || !D.fuse) return;
+  const uint32_t u1 = ~(uint32_t)*D.best;
+  const uint32_t tile = blockIdx.x - D.tile_begin;
+  const uint64_t base = (uint64_t)tile * kTile + threadIdx.x;
+#pragma unroll 4
+  for (uint32_t t = 0; t < kTileItems; ++t) {
+    const uint64_t x = base + (uint64_t)t * kSelThreads;
+    if (x < D.n && D.hslot[x] == 0xFFu)
+      D.cnt_work[x] = x == u1 ? 0u : (uint32_t)(D.cursor[x] - D.inv_off[x]) + 1u;
+  }
+  if (tile == 0 && threadIdx.x == 0) {
+    // round 0's record: the pick covers every set that holds it
+    const uint32_t c = D.cnt[u1];
+    D.seeds[0] = u1;
+    D.gains[0] = c;
+    *D.covered_total = c;
+    D.stats[1] = D.hslot[u1] == 0xFFu ? c : D.words;   // the pick's list or row, read by a plain round 0
+  }
+}
+
+// Fused first pick, hub side (blockIdx.y: instance): a hub's count is the
+// population of its row (the fill set bits for uncovered sets only), plus
+// one while unselected; the first pick's is 0.
+__global__ void __launch_bounds__(kSelThreads) bsel_first_hubs(const SelDesc *d, uint32_t ni) {
+  for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
+    const SelDesc &D = d[i];
+    if (!D.active || !D.fuse) continue;
+    const uint32_t H = D.hmeta[0] < kHeavyCap ? D.hmeta[0] : kHeavyCap;
+    const uint32_t u1 = ~(uint32_t)*D.best;
+    for (uint32_t h = 0; h < H; ++h) {
+      const uint32_t *row = D.hbits + (uint64_t)h * D.words;
+      uint32_t c = 0;
+      for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < D.words; w += gridDim.x * blockDim.x)
+        c += __popc(row[w]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
+      uint32_t *hc = D.hmeta + 1 + kHeavyCap + h;
+      if ((threadIdx.x & 31u) == 0 && c) atomicAdd(hc, c);
+      if (D.hmeta[1 + h] == u1 && blockIdx.x == 0 && threadIdx.x == 0) *hc = 0u;   // no bits: the pick's sets are covered
     }
   }
 }
@@ -352,6 +478,8 @@ cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uin
   bsel_ext_apply<<<dim3(64, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_hub_clear<<<dim3(128, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_fill<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_first_light<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_first_hubs<<<dim3(16, ny), kSelThreads, 0, s>>>(d, ni);
   return cudaGetLastError();
 }
 
@@ -510,15 +638,18 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     const SelInput &x = in[i];
     D.active = x.active ? 1u : 0u;
     D.k = x.k && x.k <= B.k_cfg[i] ? x.k : B.k_cfg[i];
-    D.set_begin = total_sets;
+    D.grp_begin = total_sets;
     D.cnt_begin = total_counted;
     D.R = D.active ? x.R : 0;
     D.ext = (D.active && x.index) ? 1u : 0u;
     D.fill_R = D.ext ? 0 : D.R;
     D.count_own = 0;
     D.count_from = 0;
+    // the first pick rides on the fill for an instance that indexes its own
+    // collection for itself (not a shared index, not multi-round)
+    D.fuse = (D.active && !D.ext && !x.index_only && x.part_n == 0 && D.k >= 1) ? 1u : 0u;
     if (!D.active) continue;
-    total_sets += D.fill_R;
+    total_sets += (D.fill_R + 31) / 32;
     SelectBuffers &b = *x.buf;
     const uint32_t *own_before = b.cnt_own;
     if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || !b.hslot ||
@@ -622,6 +753,8 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     g.bar = D.bar;
     g.part_n = in[i].part_n;
     g.part_k = in[i].part_k;
+    g.fuse = D.fuse;
+    g.inv_end = D.fuse ? D.cursor : nullptr;
   }
   CU(cudaMemcpyAsync(B.d, B.h.data(), B.ni * sizeof(SelDesc), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(B.gd, B.gh.data(), B.ni * sizeof(GreedyDesc), cudaMemcpyHostToDevice, s));
@@ -639,7 +772,7 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
   }
   CU(cudaEventRecord(ctx->ev[8], s));
   CU(cudaGraphLaunch(B.exec, s));
-  ctx->launches += 9;
+  ctx->launches += 11;
   for (size_t w = 0; w < B.wave_first.size(); ++w) {
     const uint32_t first = B.wave_first[w];
     const uint32_t count = (w + 1 < B.wave_first.size() ? B.wave_first[w + 1] : B.ni) - first;

@@ -306,6 +306,11 @@ struct GreedyDesc {
   unsigned long long *covered_total = nullptr;   // zero on entry
   unsigned long long *stats = nullptr;   // 2, zero on entry: members of newly covered sets, seed list/row words
   unsigned int *bar = nullptr;           // group barrier counter, zero on entry
+  // first pick taken by the index fill (fuse = 1): round 0's seed, gain and
+  // covered sets are already recorded, light lists hold only the sets left
+  // uncovered and end at inv_end[x]; the launch starts at round 1
+  uint32_t fuse = 0;
+  const unsigned long long *inv_end = nullptr;   // n: end of each light list (null: inv_off[x + 1])
   // multi-round IM: elements x in [r * part_n, (r + 1) * part_n) belong to
   // round r, and at most part_k seeds are taken per round (part_n = 0: no
   // partition). k is then part_k times the number of rounds.

@@ -49,29 +49,35 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
   return v;
 }
 
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // All blocks of the group have arrived `target` times in total. False if
-// the wait gave up (here or in another block).
+// the wait gave up (here or in another block). The arrival is a release
+// (after the block barrier, it publishes every write of the block) and the
+// wait an acquire; the block barrier after it passes that on to the block.
 __device__ __forceinline__ bool group_sync(unsigned int *bar, unsigned int target, unsigned int *err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    red_release_add(bar, 1u);
     const long long t0 = clock64();
     for (uint32_t polls = 0; ld_acquire(bar) < target; ++polls) {
-      if (ld_acquire(err)) {
-        ok = 0;
-        break;
-      }
-      if (clock64() - t0 > kWaitCycles) {
-        atomicOr(err, 1u);
-        ok = 0;
-        break;
+      if ((polls & 15u) == 15u) {   // the error flag and the clock: every 16 polls
+        if (ld_acquire(err)) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > kWaitCycles) {
+          atomicOr(err, 1u);
+          ok = 0;
+          break;
+        }
       }
       if (polls > 64) __nanosleep(64);   // a barrier is usually met within a few polls
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -90,17 +96,15 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-// Covers RR set j (already claimed by this warp): lowers the counts of its
-// members other than the seed u. Each lane keeps four members in flight
+// Covers the RR set stored at [b, b + len) (claimed by this warp): lowers
+// the counts of its members other than the seed u. Each lane keeps four members in flight
 // (their loads, then their hub lookups, then their decrements), since a
 // set's members are scattered over the count array and the loop is bound by
 // load latency. With no hubs (H = 0) the lookup is skipped. A light
 // member's decrement is a fire-and-forget reduction at L2; a hub's goes to
 // the block's shared-memory histogram.
-__device__ __forceinline__ uint32_t cover_set(const GreedyDesc &D, uint32_t j, uint32_t u, uint32_t H,
-                                              int *s_delta, uint32_t lane) {
-  const uint64_t b = D.rr_start[j];
-  const uint32_t len = D.rr_len[j];
+__device__ __forceinline__ uint32_t cover_members(const GreedyDesc &D, uint64_t b, uint32_t len, uint32_t u,
+                                                  uint32_t H, int *s_delta, uint32_t lane) {
   for (uint32_t q0 = 0; q0 < len; q0 += 128) {
     uint32_t x[4], hs[4];
 #pragma unroll
@@ -120,6 +124,11 @@ __device__ __forceinline__ uint32_t cover_set(const GreedyDesc &D, uint32_t j, u
     }
   }
   return len;
+}
+
+__device__ __forceinline__ uint32_t cover_set(const GreedyDesc &D, uint32_t j, uint32_t u, uint32_t H,
+                                              int *s_delta, uint32_t lane) {
+  return cover_members(D, D.rr_start[j], D.rr_len[j], u, H, s_delta, lane);
 }
 
 // Adds the block's pending hub count changes to the hub counts.
@@ -193,38 +202,77 @@ __device__ __forceinline__ void greedy_body(const GreedyDesc *d, uint32_t ni, un
   const uint32_t nwarps = nb * (kGreedyThreads / 32);
   unsigned int target = 0;
   unsigned long long newly = 0, cov_members = 0, list_words = 0;   // per thread; summed at the end
+  // The largest key of this block's light slice in the last round it was
+  // scanned (0: none yet). Counts never rise during a selection, so while
+  // its vertex keeps its count the slice's maximum is unchanged and the
+  // slice need not be read again (exact, ties included: the key is unique).
+  __shared__ unsigned long long s_light;
+  __shared__ int s_rescan;
+  if (threadIdx.x == 0) s_light = 0ull;
 
-  for (uint32_t t = 0; t < D.k; ++t) {
+  for (uint32_t t = D.fuse; t < D.k; ++t) {
     // argmax (counts change between rounds: read them at L2)
     unsigned long long m = 0;
     if (pn) {
       m = argmax_part(D, x0, x1, H, hid, hc, lb, pn, s_closed);
-    } else {
-#pragma unroll 4
-      for (uint32_t x = x0 + 4 * threadIdx.x; x < x1v; x += 4 * kGreedyThreads) {
-        const uint4 c = __ldcg(cw4 + (x >> 2));
-        m = umax(m, umax(umax(key_of(c.x, x), key_of(c.y, x + 1)), umax(key_of(c.z, x + 2), key_of(c.w, x + 3))));
+      m = warp_max(m);
+      if (lane == 0) part[wib] = m;
+      __syncthreads();
+      if (wib == 0) {
+        m = warp_max(lane < kGreedyThreads / 32 ? part[lane] : 0ull);
+        if (lane == 0) atomicMax(D.best + t, m);
       }
-      for (uint32_t x = x1v + threadIdx.x; x < x1; x += kGreedyThreads)
-        m = umax(m, key_of(__ldcg(D.cnt_work + x), x));
-      if (lb == 0)
-        for (uint32_t s = threadIdx.x; s < H; s += kGreedyThreads) m = umax(m, key_of(__ldcg(hc + s), hid[s]));
-    }
-    m = warp_max(m);
-    if (lane == 0) part[wib] = m;
-    __syncthreads();
-    if (wib == 0) {
-      m = warp_max(lane < kGreedyThreads / 32 ? part[lane] : 0ull);
-      if (lane == 0) atomicMax(D.best + t, m);
+    } else {
+      if (threadIdx.x == 0) {
+        const unsigned long long c = s_light;
+        s_rescan = c == 0ull || __ldcg(D.cnt_work + ~(uint32_t)c) != (uint32_t)(c >> 32);
+      }
+      __syncthreads();
+      if (s_rescan) {
+#pragma unroll 4
+        for (uint32_t x = x0 + 4 * threadIdx.x; x < x1v; x += 4 * kGreedyThreads) {
+          const uint4 c = __ldcg(cw4 + (x >> 2));
+          m = umax(m, umax(umax(key_of(c.x, x), key_of(c.y, x + 1)), umax(key_of(c.z, x + 2), key_of(c.w, x + 3))));
+        }
+        for (uint32_t x = x1v + threadIdx.x; x < x1; x += kGreedyThreads)
+          m = umax(m, key_of(__ldcg(D.cnt_work + x), x));
+        m = warp_max(m);
+        if (lane == 0) part[wib] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          unsigned long long b = 0;
+#pragma unroll
+          for (int w = 0; w < kGreedyThreads / 32; ++w) b = umax(b, part[w]);
+          s_light = b;
+        }
+      }
+      // the group's first block also takes the hub counts (few; read every round)
+      if (lb == 0 && H) {
+        unsigned long long h = 0;
+        for (uint32_t s = threadIdx.x; s < H; s += kGreedyThreads) h = umax(h, key_of(__ldcg(hc + s), hid[s]));
+        h = warp_max(h);
+        __syncthreads();
+        if (lane == 0) part[wib] = h;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          unsigned long long b = s_light;
+#pragma unroll
+          for (int w = 0; w < kGreedyThreads / 32; ++w) b = umax(b, part[w]);
+          atomicMax(D.best + t, b);
+        }
+      } else if (threadIdx.x == 0) {
+        atomicMax(D.best + t, s_light);
+      }
     }
     target += nb;
     if (!group_sync(D.bar, target, err)) return;
 
-    // cover
+    // cover (the seed's slot and list bounds are loaded together)
     const unsigned long long key = __ldcg(D.best + t);
     const uint32_t u = ~(uint32_t)(key & 0xFFFFFFFFull);
     const uint32_t cw = (uint32_t)(key >> 32);
     const uint32_t us = D.hslot[u];
+    const uint64_t i0 = D.inv_off[u], i1 = D.inv_end ? D.inv_end[u] : D.inv_off[u + 1];
     if constexpr (kPart) {
       if (pn && threadIdx.x == 0) {   // this round's seed counts toward its round (read by the next argmax)
         const uint32_t r = u / pn;
@@ -240,11 +288,15 @@ __device__ __forceinline__ void greedy_body(const GreedyDesc *d, uint32_t ni, un
         hc[us] = 0u;
     }
     if (us == 0xFFu) {
-      // light seed: its inverted list, one set per warp
-      const uint64_t i0 = D.inv_off[u], i1 = D.inv_off[u + 1];
+      // light seed: its inverted list, one set per warp. Lane 0 claims the
+      // set on the covered bitmap and the warp follows its answer (lanes that
+      // read the bitmap themselves could see a bit lane 0 has just set); the
+      // set's place is loaded in the same round trip as the claim.
       for (uint64_t p = i0 + gwarp; p < i1; p += nwarps) {
         const uint32_t j = D.inv[p];
         if (j >= D.R) continue;   // beyond this instance's prefix of a shared index
+        const uint64_t sb = D.rr_start[j];
+        const uint32_t sl = D.rr_len[j];
         uint32_t fresh = 0;
         if (lane == 0) {
           const uint32_t bit = 1u << (j & 31u);
@@ -252,7 +304,7 @@ __device__ __forceinline__ void greedy_body(const GreedyDesc *d, uint32_t ni, un
         }
         fresh = __shfl_sync(kFullMask, fresh, 0);
         if (!fresh) continue;
-        const uint32_t len = cover_set(D, j, u, H, s_delta, lane);
+        const uint32_t len = cover_members(D, sb, sl, u, H, s_delta, lane);
         if (lane == 0) {
           newly += 1;
           cov_members += len;
