@@ -493,8 +493,22 @@ def algorithmic_bytes(cnt: np.ndarray, indeg: np.ndarray) -> float:
     return float(cnt.astype(np.float64).sum() * 24.0)
 
 
+def issue_slots(calls, kern_s, inst_per_call, sms, sm_mhz):
+    """Issue-slot view of the IC sampler: warp instructions issued per second
+    (the Philox calls of the timed runs times the warp instructions per call
+    that one ncu capture of both sampling kernels counted) against the SMs'
+    issue rate, one warp instruction per cycle in each of 4 schedulers."""
+    if not (kern_s > 0 and inst_per_call and sms and sm_mhz):
+        return None
+    achieved = calls * inst_per_call / kern_s / 1e9          # G warp instructions / s
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_philox_call": inst_per_call, "sms": sms, "sm_mhz": sm_mhz,
+            "peak_kind": "4 issue slots per SM per cycle at the sampled SM clock"}
+
+
 def roofline(kname, coins, calls, alg_bytes, members, kern_s, n_launch, philox_calls_per_s, hbm_peak, peak_kind,
-             traffic, large_launches):
+             traffic, large_launches, issue=None):
     """Roofline position of the dominant sampling kernel.
 
     IC (weighted cascade): the in-edge scans read no edge data; the work is
@@ -519,6 +533,8 @@ def roofline(kname, coins, calls, alg_bytes, members, kern_s, n_launch, philox_c
                 gcoins_per_s=coins / kern_s / 1e9 if kern_s > 0 else 0.0,
                 hbm_view={"algorithmic_gbs": alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0, "peak_gbs": hbm_peak,
                           "peak_kind": peak_kind})
+    if issue is not None:
+        base["issue_slots"] = issue
     return base
 
 
@@ -711,6 +727,12 @@ def run_ours(args):
         if tr is not None:
             per_unit, unit = tr
             traffic = per_unit * (rr_sets / n_launch) if unit == "rr_set" else None
+        clocks = clk.summary()
+        issue = None
+        ir = traffic_record("sample_ic_issue") if kname == "sample_ic_kernel" else None
+        if ir is not None and ir[1] == "warp_inst_per_philox_call" and clocks:
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            issue = issue_slots(calls, kern_s, ir[0], sms, clocks["sm_mhz"])
         line = {
             "metric": METRIC, "value": units / secs, "unit": "RR-sets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -724,9 +746,9 @@ def run_ours(args):
                     "load_ms": e2e_load, "run_ms": e2e_run},
             "gpu_launches": launches,
             "roofline": roofline(kname, coins, calls, alg_bytes, members_total, kern_s, n_launch, philox_calls_per_s,
-                                 hbm_peak, peak_kind, traffic, tk["large_launches"]),
+                                 hbm_peak, peak_kind, traffic, tk["large_launches"], issue),
             "select_roofline": select_roofline(sel, hbm_peak, peak_kind),
-            "clocks": clk.summary(),
+            "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, budget_s=args.cpu_budget, single_core_s=args.cpu_single_budget)
@@ -767,6 +789,8 @@ def run_case(args):
     t_s = time.perf_counter() - t0
     out = {"case": args.case, "count": args.count, "sample_s": t_s, "timings": ctx.timings(),
            "members": ctx.rr_count()[1]}
+    if model == GIM_IC:   # the Philox calls the sampled collection needed (see philox_calls)
+        out["philox_calls"] = philox_calls(ctx.coverage(), g.indegree(), row_probability(g))
     if args.case == "select":
         t0 = time.perf_counter()
         s, gains, cov = ctx.select_seeds(WORKLOAD["k"])

@@ -62,6 +62,7 @@ struct gim_server {
   uint32_t max_k = 0;
   uint64_t budget = 0;
   std::map<std::pair<int, uint64_t>, gim_ctx *> pools;   // (model, seed) -> RR pool sharing the graph
+  std::map<gim_ctx *, uint64_t> pool_used;               // pool -> the last round a query read it
   std::vector<SelectBuffers> slot_buf;
   std::vector<Query *> slot_q;
   // shared indexes: instance max_active + i of ms builds the index of pool
@@ -123,12 +124,57 @@ gim_status make_view(gim_server *S, gim_ctx **out) {
   return GIM_OK;
 }
 
-gim_status get_pool(gim_server *S, int model, uint64_t seed, gim_ctx **out) {
+// Pools no admitted query reads, least recently used first.
+std::vector<std::pair<std::pair<int, uint64_t>, gim_ctx *>> idle_pools(gim_server *S,
+                                                                       const std::vector<Query *> &active) {
+  std::vector<std::pair<std::pair<int, uint64_t>, gim_ctx *>> out;
+  for (auto &kv : S->pools) {
+    bool used = false;
+    for (const Query *q : active) used |= q->pool == kv.second;
+    if (!used) out.push_back(kv);
+  }
+  std::sort(out.begin(), out.end(), [&](const auto &a, const auto &b) { return S->pool_used[a.second] < S->pool_used[b.second]; });
+  return out;
+}
+
+// A pool leaves the server: its shared index (if any) is dropped with it.
+void forget_pool(gim_server *S, gim_ctx *c) {
+  for (size_t i = 0; i < S->index_pool.size(); ++i)
+    if (S->index_pool[i] == c) {
+      S->index_pool[i] = nullptr;
+      S->index_R[i] = 0;
+    }
+  S->pool_used.erase(c);
+}
+
+gim_status get_pool(gim_server *S, int model, uint64_t seed, const std::vector<Query *> &active, uint64_t used,
+                    gim_ctx **out) {
   auto key = std::make_pair(model, seed);
   auto it = S->pools.find(key);
   if (it != S->pools.end()) {
     *out = it->second;
     return GIM_OK;
+  }
+  // A new (model, seed): once the server holds as many pools as slots, or
+  // half its memory budget, the least recently used idle pool is emptied
+  // and reused (its store, counts and tables stay allocated), so queries
+  // with their own seeds do not allocate a pool each.
+  if (S->pools.size() >= S->max_active || used > S->budget / 2) {
+    auto idle = idle_pools(S, active);
+    if (!idle.empty()) {
+      gim_ctx *c = idle.front().second;
+      S->pools.erase(idle.front().first);
+      forget_pool(S, c);
+      const gim_status st = gim_reset_rr(c);
+      if (st != GIM_OK) {
+        gim_destroy(c);
+        return st;
+      }
+      S->pools[key] = c;
+      S->pool_used[c] = S->rounds;
+      *out = c;
+      return GIM_OK;
+    }
   }
   gim_ctx *c = nullptr;
   gim_status st = make_view(S, &c);
@@ -140,6 +186,7 @@ gim_status get_pool(gim_server *S, int model, uint64_t seed, gim_ctx **out) {
     return GIM_ERR_OOM;
   }
   S->pools[key] = c;
+  S->pool_used[c] = S->rounds;
   *out = c;
   return GIM_OK;
 }
@@ -156,6 +203,7 @@ gim_status round_once(gim_server *S, std::vector<Query *> &active) {
     q->Rq = std::max(q->Rq, t);
     uint64_t &pt = target[q->pool];
     pt = std::max(pt, q->Rq);
+    S->pool_used[q->pool] = S->rounds;
   }
   const auto t0 = Clock::now();
   std::vector<SampleJobH> jobs;
@@ -181,12 +229,19 @@ gim_status round_once(gim_server *S, std::vector<Query *> &active) {
   // with room among the shared indexes gets one index over all its sets,
   // rebuilt only when the pool has grown; a query whose prefix is at least a
   // quarter of its pool uses it (its lists read up to the prefix) instead of
-  // indexing its prefix itself
+  // indexing its prefix itself. A pool read by one query only gets no shared
+  // index: that query indexes its prefix itself, with the first pick taken
+  // during the fill
   const uint32_t ni = (uint32_t)S->index_buf.size();
   std::vector<SelInput> in(S->max_active + ni);
-  std::map<gim_ctx *, int> pool_index;
+  std::map<gim_ctx *, int> pool_index, readers;
+  for (Query *q : active) readers[q->pool]++;
   for (Query *q : active) {
     if (pool_index.count(q->pool)) continue;
+    if (readers[q->pool] < 2) {
+      pool_index[q->pool] = -1;
+      continue;
+    }
     int ix = -1;
     for (uint32_t i = 0; i < ni; ++i)
       if (S->index_pool[i] == q->pool) ix = (int)i;
@@ -284,10 +339,22 @@ void worker_main(gim_server *S) {
         q->projected = projected_bytes(S, *q);
         uint64_t pending = 0;
         for (Query *a : active) pending += a->projected;
-        if (!active.empty() && used + pending + q->projected > S->budget) break;
+        if (!active.empty() && used + pending + q->projected > S->budget) {
+          // free idle pools (least recently used first) before holding the query back
+          auto idle = idle_pools(S, active);
+          for (auto &kv : idle) {
+            if (kv.first == std::make_pair((int)q->p.model, q->p.seed)) continue;   // the query's own pool
+            used -= std::min(used, pool_bytes(kv.second));
+            S->pools.erase(kv.first);
+            forget_pool(S, kv.second);
+            gim_destroy(kv.second);
+            if (used + pending + q->projected <= S->budget) break;
+          }
+          if (used + pending + q->projected > S->budget) break;
+        }
         S->waiting.pop_front();
         gim_ctx *pool = nullptr;
-        const gim_status st = get_pool(S, q->p.model, q->p.seed, &pool);
+        const gim_status st = get_pool(S, q->p.model, q->p.seed, active, used, &pool);
         if (st != GIM_OK) {
           q->status = st;
           q->done = true;

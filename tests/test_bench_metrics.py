@@ -60,6 +60,14 @@ def test_roofline_lines():
                         large_launches=1)
     assert lt["bound"] == "hbm" and lt["unit"] == "GB/s"
     assert lt["achieved"] == pytest.approx(36.0 * 1e8 / 0.02 / 1e9)
+    iss = bench.issue_slots(calls=6e8, kern_s=0.01, inst_per_call=7.0, sms=152, sm_mhz=2070.0)
+    assert iss["achieved"] == pytest.approx(6e8 * 7.0 / 0.01 / 1e9)
+    assert iss["peak"] == pytest.approx(152 * 4 * 2.07) and iss["frac"] == pytest.approx(420.0 / (152 * 4 * 2.07))
+    assert bench.issue_slots(6e8, 0.0, 7.0, 152, 2070.0) is None
+    with_issue = bench.roofline("sample_ic_kernel", coins=8e9, calls=6e8, alg_bytes=1e9, members=5e7, kern_s=0.01,
+                                n_launch=4, philox_calls_per_s=4.8e11, hbm_peak=6644.1, peak_kind="measured",
+                                traffic=None, large_launches=1, issue=iss)
+    assert with_issue["issue_slots"] is iss and with_issue["unit"] == "G Philox calls/s"
     sel = bench.select_roofline({"kernel_ms": 5.0, "bytes": 6.6441e9, "calls": 4}, 6644.1, "measured")
     assert sel["achieved"] == pytest.approx(1328.82) and sel["frac"] == pytest.approx(0.2)
     assert sel["ms_per_selection"] == pytest.approx(1.25)
