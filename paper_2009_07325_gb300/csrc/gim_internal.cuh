@@ -106,6 +106,33 @@ __device__ __forceinline__ uint32_t draw_root(PhiloxKey key, uint32_t jlo, uint3
 }
 
 // ---------------------------------------------------------------------------
+// LT thresholds in exact integer arithmetic (graph preparation and the walk).
+// ---------------------------------------------------------------------------
+// fp32 weight w = M * 2^E exactly (M < 2^24); returns E, or INT_MAX for w = 0.
+__device__ __forceinline__ int ulp_exponent(float w, uint32_t *mant) {
+  const uint32_t b = __float_as_uint(w);
+  const uint32_t ef = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (ef == 0 && m == 0) {
+    *mant = 0;
+    return 0x7FFFFFFF;
+  }
+  *mant = ef ? (m | 0x800000u) : m;
+  return ef ? (int)ef - 150 : -149;
+}
+
+// round_half_up(Q * 2^k), clamped to 2^32, for Q < 2^53.
+__device__ __forceinline__ unsigned long long lt_round_int(unsigned long long Q, int k) {
+  unsigned long long c;
+  if (k >= 0)
+    c = Q << k;                                   // k <= 9 for weights <= 1: no overflow
+  else if (k < -60)
+    c = 0ull;                                     // Q * 2^k < 2^-7
+  else
+    c = (Q + (1ull << (-k - 1))) >> (-k);
+  return c > 4294967296ull ? 4294967296ull : c;
+}
+
+// ---------------------------------------------------------------------------
 // Device-resident graph (in-edge CSR by target).
 // ---------------------------------------------------------------------------
 struct DevGraph {

@@ -39,18 +39,6 @@ __device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long l
   return v;
 }
 
-// fp32 weight w = M * 2^E exactly (M < 2^24); returns E, or INT_MAX for w = 0.
-__device__ __forceinline__ int ulp_exponent(float w, uint32_t *mant) {
-  const uint32_t b = __float_as_uint(w);
-  const uint32_t ef = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
-  if (ef == 0 && m == 0) {
-    *mant = 0;
-    return 0x7FFFFFFF;
-  }
-  *mant = ef ? (m | 0x800000u) : m;
-  return ef ? (int)ef - 150 : -149;
-}
-
 __device__ __forceinline__ unsigned long long lt_round(double P) {
   const double x = __dmul_rn(P, 4294967296.0);
   const double f = floor(x);
@@ -147,18 +135,6 @@ __global__ void __launch_bounds__(256) prep_big_rows_kernel(const uint32_t *__re
 // kSmallRow in-edges take one thread each (prep_lt_kernel); the others are
 // listed for a block each (prep_lt_big_kernel), which scans 256 in-edges
 // at a time.
-
-// round_half_up(Q * 2^k), clamped to 2^32, for Q < 2^53.
-__device__ __forceinline__ unsigned long long lt_round_int(unsigned long long Q, int k) {
-  unsigned long long c;
-  if (k >= 0)
-    c = Q << k;                                   // k <= 9 for weights <= 1: no overflow
-  else if (k < -60)
-    c = 0ull;                                     // Q * 2^k < 2^-7
-  else
-    c = (Q + (1ull << (-k - 1))) >> (-k);
-  return c > 4294967296ull ? 4294967296ull : c;
-}
 
 // The row fix-ups and the LT-validity flag from the row total P.
 __device__ __forceinline__ void lt_row_end(double P, uint32_t s, uint32_t e, uint64_t *cum, unsigned int &bad) {

@@ -820,6 +820,40 @@ __device__ __forceinline__ uint32_t lt_pick(const uint64_t *__restrict__ cum, ui
   return b ? lo + (uint32_t)(__ffs(b) - 1) : hi;
 }
 
+// The in-edge an equal-weight row [s, e) (d = e - s in-edges, common fp32
+// weight wbits) chooses for the draw U: the first i with U < T(i), or d for
+// none. For such a row the LT preparation stores the exact integer
+// thresholds T(i) = round_half_up((i+1)·M·2^(E+32)), clamped to 2^32 (weight
+// M·2^E), except that the last becomes 2^32 when the row's total is within
+// 1e-6 of 1. So the walk computes them from the weight instead of loading
+// them: it starts from the fp32 guess floor(U / (w·2^32)), moves to the
+// first threshold above U, and reads the stored last threshold only when it
+// reaches the row's end. Returns ~0u when the guess does not settle within a
+// few steps, or when the prefix sums would leave the exact range (rows of
+// 2^29 in-edges or more); the caller then searches the stored thresholds.
+__device__ __forceinline__ uint32_t lt_equal_pick(uint32_t wbits, uint32_t s, uint32_t e, uint32_t U,
+                                                  const uint64_t *__restrict__ cum) {
+  const uint32_t d = e - s;
+  uint32_t mant;
+  const int ex = ulp_exponent(__uint_as_float(wbits), &mant);
+  if (mant == 0u) return d;                       // zero weights: no in-edge is ever chosen
+  if ((unsigned long long)d * mant >= (1ull << 53)) return ~0u;
+  const int k = ex + 32;
+  const float w = __uint_as_float(wbits);
+  float gf = floorf(__uint2float_rn(U) * __frcp_rn(w * 4294967296.0f));
+  if (!(gf < (float)(d - 1))) gf = (float)(d - 1);
+  uint32_t g = gf > 0.0f ? (uint32_t)gf : 0u;
+  const unsigned long long u64 = U;
+  // T(g - 1) = lt_round_int(g·M, k), T(g) = lt_round_int((g+1)·M, k)
+  for (int it = 0; it < 8 && g > 0 && u64 < lt_round_int((unsigned long long)g * mant, k); ++it) --g;
+  for (int it = 0; it < 8 && g + 1 < d && u64 >= lt_round_int((unsigned long long)(g + 1) * mant, k); ++it) ++g;
+  if ((g > 0 && u64 < lt_round_int((unsigned long long)g * mant, k)) ||
+      (g + 1 < d && u64 >= lt_round_int((unsigned long long)(g + 1) * mant, k)))
+    return ~0u;
+  if (g + 1 < d) return g;                        // T(g - 1) <= U < T(g)
+  return u64 < cum[e - 1] ? g : d;                // the last threshold may be raised to 2^32
+}
+
 // The in-edge LT chooses at row [s, e) for the draw U: its index, or e for
 // none (the first a with U < cum[a]; Sec. III-G), and in u its source.
 // When every in-edge of the row has the same weight w (rw != kPerEdge) the
@@ -831,28 +865,12 @@ __device__ __forceinline__ uint32_t lt_pick(const uint64_t *__restrict__ cum, ui
 // for rows of unequal weights) the 33-way search of lt_pick decides.
 __device__ __forceinline__ uint32_t lt_choose(const uint64_t *__restrict__ cum, const uint32_t *__restrict__ src,
                                               uint32_t s, uint32_t e, uint32_t wbits, uint32_t U, uint32_t &u) {
-  const uint32_t lane = lane_id();
   if (wbits != kPerEdge) {
-    const uint32_t d = e - s;
-    // fp32 guess (relative error ~2^-22, far inside the window for any row
-    // below 2^20 in-edges; fp64 would run on the GPU's slow double pipe)
-    const float w = __uint_as_float(wbits);
-    float gf = w > 0.0f ? floorf(__uint2float_rn(U) * __frcp_rn(w * 4294967296.0f)) : (float)(d - 1);
-    if (!(gf < (float)(d - 1))) gf = (float)(d - 1);
-    const uint32_t g = gf > 0.0f ? (uint32_t)gf : 0u;
-    const uint32_t w0 = g > 15u ? g - 15u : 0u;                 // window [w0, w0 + 32) within the row
-    const uint32_t p = s + w0 + lane;
-    const bool in = p < e;
-    const bool hit = in && (uint64_t)U < cum[p];
-    const uint32_t sp = in ? src[p] : 0u;
-    const uint32_t b = __ballot_sync(kFullMask, hit);
-    const bool tail = s + w0 + 32u >= e;                       // the window reaches the row's end
-    if (b != 0u && ((b & 1u) == 0u || w0 == 0u)) {
-      const int f = __ffs(b) - 1;
-      u = __shfl_sync(kFullMask, sp, f);
-      return s + w0 + (uint32_t)f;
+    const uint32_t i = lt_equal_pick(wbits, s, e, U, cum);   // warp-uniform
+    if (i != ~0u) {
+      if (i < e - s) u = src[s + i];
+      return s + i;
     }
-    if (b == 0u && tail) return e;
   }
   const uint32_t a = lt_pick(cum, s, e, U);
   if (a < e) u = src[a];
@@ -991,34 +1009,17 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
       U = philox10(x, kTagStep, id_lo(V, j), V.jhi, V.key).x;
       if (e == s) ended = true;
     }
-    // window of eight thresholds around the guess (rows of equal weights)
+    // rows of equal weights: the chosen in-edge from the computed thresholds,
+    // then only its source is read (all eight lanes load the same word)
     bool need = active && !ended;          // still looking for the chosen edge
-    uint32_t w0 = 0;
-    bool use_window = need && wb != kPerEdge;
-    if (use_window) {
-      const uint32_t d = e - s;
-      const float w = __uint_as_float(wb);
-      float gf = w > 0.0f ? floorf(__uint2float_rn(U) * __frcp_rn(w * 4294967296.0f)) : (float)(d - 1);
-      if (!(gf < (float)(d - 1))) gf = (float)(d - 1);
-      const uint32_t g = gf > 0.0f ? (uint32_t)gf : 0u;
-      w0 = g > 3u ? g - 3u : 0u;
-    }
-    {
-      const uint32_t p = s + w0 + gl;
-      const bool in = use_window && p < e;
-      const bool hit = in && (uint64_t)U < V.cum[p];
-      const uint32_t sp = in ? V.src[p] : 0u;
-      const uint32_t b = (__ballot_sync(kFullMask, hit) >> lead) & 0xFFu;
-      const uint32_t f = b ? (uint32_t)(__ffs(b) - 1) : 0u;
-      const uint32_t us = __shfl_sync(kFullMask, sp, lead + f);
-      if (use_window) {
-        if (b != 0u && ((b & 1u) == 0u || w0 == 0u)) {
-          u = us;
-          need = false;
-        } else if (b == 0u && s + w0 + kLtLanes >= e) {
+    if (need && wb != kPerEdge) {
+      const uint32_t i = lt_equal_pick(wb, s, e, U, V.cum);
+      if (i != ~0u) {
+        need = false;
+        if (i < e - s)
+          u = V.src[s + i];
+        else
           ended = true;                     // no edge chosen
-          need = false;
-        }
       }
     }
     // otherwise a 9-way search: the answer lies in [lo, hi], hi = e meaning
