@@ -695,8 +695,9 @@ def run_ours(args):
     off_p, src_p, w_p = (t.numpy() for t in pinned)   # the tensors stay referenced: the memory stays pinned
     h2d = off_p.nbytes + src_p.nbytes + w_p.nbytes
     e2e_t, e2e_units = 0.0, 0
-    ctx.graph_load(g.n, off_p, src_p, w_p)    # untimed warm-up: the first load allocates the graph arrays
-    run_once()
+    for _ in range(2):   # untimed warm-up: the first two loads allocate both sets of graph arrays
+        ctx.graph_load(g.n, off_p, src_p, w_p)
+        run_once()
     e2e_load, e2e_run = [], []
     gc.collect()
     gc.disable()   # as timeit does: no interpreter garbage-collection pauses inside the timed iterations
