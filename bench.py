@@ -258,6 +258,7 @@ def batch_measure(local, steps, warmup, count=256):
     del graphs
     params = [p for _, p in specs]
     batch_budget, _ = binding.autotune(ctxs, params, 2000)        # schedule for the batch as a whole
+    batch_schedule = ctxs[0].schedule()
     for _ in range(max(1, warmup)):
         res = binding.batch_imm(ctxs, params)
     ctxs[0].reset_timings()
@@ -275,7 +276,11 @@ def batch_measure(local, steps, warmup, count=256):
     batched_seeds = [r["seeds"].tolist() for r in res]
     # the plain path: one gim_imm per instance, back to back, each instance
     # with the schedule the autotuner picks for it alone (one warm-up pass)
-    plain_budgets = [binding.autotune([c], [p], 2000)[0] for c, p in zip(ctxs, params)]
+    plain_schedules = []
+    for c, p in zip(ctxs, params):
+        binding.autotune([c], [p], 2000)
+        plain_schedules.append(c.schedule())
+    plain_budgets = [x["group_budget"] for x in plain_schedules]
     for c, p in zip(ctxs, params):
         c.imm(*p)
     torch.cuda.synchronize()
@@ -304,8 +309,10 @@ def batch_measure(local, steps, warmup, count=256):
            "batched_kernel_ms_per_batch": {"common": tb["kernel_ms"] / max(1, steps),
                                            "large": tb["large_ms"] / max(1, steps)},
            "rounds": max(r["lb_rounds"] for r in res) + 1,
-           "tuning": {"batch_group_budget": batch_budget,
-                      "plain_group_budgets": sorted(set(plain_budgets)), "by": "gim_autotune"},
+           "tuning": {"batch_group_budget": batch_budget, "batch_schedule": batch_schedule,
+                      "plain_group_budgets": sorted(set(plain_budgets)),
+                      "plain_schedules": sorted({tuple(sorted(x.items())) for x in plain_schedules}),
+                      "by": "gim_autotune"},
            "gpu_launches": launches, "graph_generation_s": t_gen, "clocks": clk.summary()}
     for c in ctxs:
         c.close()
@@ -638,6 +645,7 @@ def run_ours(args):
     else:
         budget, _ = binding.autotune([ctx], [(mdl, k, eps, ell, seed)], 20000)   # schedule for this profile
         tuned_by = "gim_autotune"
+    ctx_schedule = ctx.schedule()
     T = WORKLOAD.get("rounds", 0)
 
     def run_once():
@@ -701,7 +709,7 @@ def run_ours(args):
     e2e_load, e2e_run = [], []
     gc.collect()
     gc.disable()   # as timeit does: no interpreter garbage-collection pauses inside the timed iterations
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.graph_load(g.n, off_p, src_p, w_p)
@@ -740,10 +748,10 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas{world}", l2="flushed between steps (512 MiB write)"),
             "imm_s": secs / args.steps, "theta": thetas[-1], "rr_sets_per_step": rr_sets / args.steps,
-            "tuning": {"group_budget": budget, "by": tuned_by},
+            "tuning": dict(ctx_schedule, by=tuned_by),
             "sample_ms_per_step": sample_ms / args.steps, "select_ms_per_step": select_ms / args.steps,
             "e2e": {"value": e2e_u / e2e_s, "unit": "RR-sets/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 3)),
+                    "d2h_bytes_per_step": d2h, "imm_s": e2e_s / max(1, min(args.steps, 5)),
                     "load_ms": e2e_load, "run_ms": e2e_run},
             "gpu_launches": launches,
             "roofline": roofline(kname, coins, calls, alg_bytes, members_total, kern_s, n_launch, philox_calls_per_s,

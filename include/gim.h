@@ -310,9 +310,13 @@ gim_status gim_server_poll(gim_server *srv, uint64_t ticket, uint32_t timeout_ms
 gim_status gim_server_stats(gim_server *srv, double out[8]);
 void gim_server_stop(gim_server *srv);
 
-/* Options of a context. GIM_OPT_GROUP_BUDGET and GIM_OPT_LARGE_PASS_BYTES
-   are tuning knobs: they change speed, never results. GIM_OPT_FRESH_FINAL
-   selects a variant of IMM and changes its results. */
+/* Options of a context. GIM_OPT_GROUP_BUDGET, GIM_OPT_LARGE_PASS_BYTES,
+   GIM_OPT_FRONTIER_BATCH, GIM_OPT_CHUNK_GROUPS and GIM_OPT_QUEUE_CAP are
+   tuning knobs: they change speed, never results (every RR set is a function
+   of (graph, model, seed, rr_id) alone). GIM_OPT_FRESH_FINAL selects a
+   variant of IMM and changes its results. A launch that serves several
+   contexts (gim_batch_imm, the server) takes the knobs of its first
+   context. */
 typedef enum {
   /* In-edge groups (4 in-edges each) one RR set may scan in the warp-per-set
      IC pass before it is handed to the block-per-set pass. Default 16384. */
@@ -333,29 +337,47 @@ typedef enum {
      LB are unchanged; rr_count = theta. The collection keeps its counter
      base until it is reset. The server always runs IMM as published.
      0 (default): reuse. Values other than 0 and 1 are rejected. */
-  GIM_OPT_FRESH_FINAL = 2
+  GIM_OPT_FRESH_FINAL = 2,
+  /* Frontier vertices the block-per-set IC pass expands per block step (a
+     level-synchronous batch): 32 .. 256, a multiple of 32. Default 256. */
+  GIM_OPT_FRONTIER_BATCH = 3,
+  /* In-edge groups (4 in-edges) per work chunk of the block-per-set IC
+     pass: 64 .. 4096, a multiple of 64. A row with p <= 2^-8 is cut into
+     chunks of half as many super-groups (16 in-edges), i.e. twice the
+     in-edges. Default 512 (2048 in-edges; 4096 in screened rows). */
+  GIM_OPT_CHUNK_GROUPS = 4,
+  /* Members an RR set may reach in the warp-per-set IC pass before it is
+     handed to the block-per-set pass (the warp's queue): 256 .. 4096, a
+     multiple of 32. Default 4096. */
+  GIM_OPT_QUEUE_CAP = 5
 } gim_option;
 
 /* Sets an option. Errors: GIM_ERR_ARG (unknown option, value 0 for the
-   tuning knobs, value above 1 for GIM_OPT_FRESH_FINAL). */
+   tuning knobs or outside a knob's stated range, value above 1 for
+   GIM_OPT_FRESH_FINAL). */
 gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value);
 
 /* Reads a tuning knob into *value. */
 gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value);
 
 /*
- * Autotuner: picks GIM_OPT_GROUP_BUDGET - how long one warp keeps an RR set
- * before a 256-thread block takes it over, i.e. warps per RR set for heavy
- * sets - for a workload, by timing the sampling of `sample_sets` RR sets
- * per instance under each candidate (4096 .. 2^30 groups) exactly as
- * gim_batch_imm (n_inst > 1) or gim_imm (n_inst = 1) would launch it. The
+ * Autotuner: picks the sampling schedule of a workload - GIM_OPT_GROUP_BUDGET
+ * (how long one warp keeps an RR set before a 256-thread block takes it
+ * over, i.e. warps per RR set for heavy sets), then GIM_OPT_CHUNK_GROUPS
+ * (the block pass's work chunk), GIM_OPT_FRONTIER_BATCH (its frontier batch)
+ * and GIM_OPT_QUEUE_CAP (the warp pass's frontier buffer), one knob at a time
+ * with the others at their best so far - by timing the sampling of
+ * `sample_sets` RR sets per instance under each candidate exactly as
+ * gim_batch_imm (n_inst > 1) or gim_imm (n_inst = 1) would launch it (the
+ * paper sizes its shared queue and grid by hand, Sec. III-F and IV-G). The
  * choice is cached for the process under the workload's degree profile
  * (log2 of n, of mean and of maximum in-degree, the model, log2 of n_inst),
- * so later calls with the same profile only read the cache. The chosen value
- * is set on every context; their RR collections are emptied.
+ * so later calls with the same profile only read the cache. The chosen
+ * values are set on every context; their RR collections are emptied.
  *   ctxs, n_inst, params: as for gim_batch_imm (params give model and seed).
- *   budget_out: nullable; the chosen budget. measured_out: nullable; 1 if
- *   this call timed the candidates, 0 if it used the cache.
+ *   budget_out: nullable; the chosen budget (the other knobs: gim_get_option).
+ *   measured_out: nullable; 1 if this call timed the candidates, 0 if it
+ *   used the cache.
  */
 gim_status gim_autotune(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_params *params, uint64_t sample_sets,
                         uint64_t *budget_out, int *measured_out);

@@ -20,6 +20,11 @@ GIM_IC, GIM_LT = 0, 1
 GIM_OPT_GROUP_BUDGET = 0
 GIM_OPT_LARGE_PASS_BYTES = 1
 GIM_OPT_FRESH_FINAL = 2
+GIM_OPT_FRONTIER_BATCH = 3
+GIM_OPT_CHUNK_GROUPS = 4
+GIM_OPT_QUEUE_CAP = 5
+SCHEDULE_OPTIONS = {"group_budget": GIM_OPT_GROUP_BUDGET, "chunk_groups": GIM_OPT_CHUNK_GROUPS,
+                    "frontier_batch": GIM_OPT_FRONTIER_BATCH, "queue_cap": GIM_OPT_QUEUE_CAP}
 STATUS = {0: "GIM_OK", 1: "GIM_ERR_ARG", 2: "GIM_ERR_OOM", 3: "GIM_ERR_CUDA", 4: "GIM_ERR_TIMEOUT",
           5: "GIM_ERR_STATE"}
 
@@ -277,6 +282,10 @@ class Context:
 
     def set_option(self, opt: int, value: int):
         self._check(self.L.gim_set_option(self.h, opt, value), "gim_set_option")
+
+    def schedule(self) -> dict:
+        """The sampling schedule's knobs (gim_get_option of each)."""
+        return {name: self.get_option(opt) for name, opt in SCHEDULE_OPTIONS.items()}
 
     def get_option(self, opt: int) -> int:
         v = ctypes.c_uint64(0)

@@ -513,6 +513,18 @@ gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value) {
     ctx->fresh_final = value == 1;
     return GIM_OK;
   }
+  if (opt == GIM_OPT_FRONTIER_BATCH && value >= 32 && value <= 256 && value % 32 == 0) {
+    ctx->frontier_batch = (uint32_t)value;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_CHUNK_GROUPS && value >= 64 && value <= 4096 && value % 64 == 0) {
+    ctx->chunk_groups = (uint32_t)value;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_QUEUE_CAP && value >= 256 && value <= kQueueCap && value % 32 == 0) {
+    ctx->queue_cap = (uint32_t)value;
+    return GIM_OK;
+  }
   return set_err(ctx, GIM_ERR_ARG, "unknown option or value out of range");
 }
 
@@ -524,6 +536,18 @@ gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value) {
   }
   if (opt == GIM_OPT_LARGE_PASS_BYTES) {
     *value = ctx->big_budget;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_FRONTIER_BATCH) {
+    *value = ctx->frontier_batch;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_CHUNK_GROUPS) {
+    *value = ctx->chunk_groups;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_QUEUE_CAP) {
+    *value = ctx->queue_cap;
     return GIM_OK;
   }
   if (opt == GIM_OPT_FRESH_FINAL) {

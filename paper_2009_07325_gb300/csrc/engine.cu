@@ -317,7 +317,11 @@ gim_status run_one(gim_ctx *ctx, DeviceShared &D, int model, std::vector<SampleJ
   L.deferred = P.out;
   L.deferred_cap = D.def_cap / 2;
   L.ctl = D.d_ctl;
-  L.group_budget = P.large ? 0xFFFFFFFFu : ctx->group_budget;   // the first context's knob serves the launch
+  L.group_budget = P.large ? 0xFFFFFFFFu : ctx->group_budget;   // the first context's knobs serve the launch
+  // the knobs as gim_set_option admits them (kernels index shared arrays by the batch)
+  L.queue_cap = std::min<uint32_t>(std::max<uint32_t>(ctx->queue_cap, 256u), kQueueCap);
+  L.batch = std::min<uint32_t>(std::max<uint32_t>(ctx->frontier_batch, 32u), (uint32_t)kBigBlock);
+  L.chunk_groups = std::max<uint32_t>(ctx->chunk_groups, 64u);
   L.item_slots = P.list_slots;
   L.deferred_slots = P.out_slots;
   L.lt_ovf = D.lt_ovf;

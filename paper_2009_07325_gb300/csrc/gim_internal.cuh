@@ -212,6 +212,9 @@ struct SampleLaunch {
   unsigned long long deferred_cap;
   SampleCtl *ctl;
   uint32_t group_budget;             // common pass: edge groups (4 in-edges) a set may scan
+  uint32_t queue_cap;                // common pass: members a set may reach (<= kQueueCap)
+  uint32_t batch;                    // block pass: frontier vertices per block step (<= 256)
+  uint32_t chunk_groups;             // block pass: groups per chunk (a multiple of 64)
   // LT walks that outgrow the common pass's path keep it in an overflow slot
   // (kLtGroupPath entries) so that the large pass continues them instead of
   // starting over: items[i] / deferred[d] have slot item_slots[i] /
@@ -524,6 +527,9 @@ struct gim_ctx {
 
   bool shared_held = false;       // holds a reference on the device's shared scratch
   uint32_t group_budget = 1u << 14;   // GIM_OPT_GROUP_BUDGET
+  uint32_t frontier_batch = 256;      // GIM_OPT_FRONTIER_BATCH
+  uint32_t chunk_groups = 512;        // GIM_OPT_CHUNK_GROUPS
+  uint32_t queue_cap = 4096;          // GIM_OPT_QUEUE_CAP
   uint64_t big_budget = 16ull << 30;  // GIM_OPT_LARGE_PASS_BYTES
   bool fresh_final = false;           // GIM_OPT_FRESH_FINAL
 

@@ -191,6 +191,9 @@ gim_status mrim_sample(gim_ctx *ctx, int model, uint64_t seed, uint64_t count) {
     v->lt_ok = ctx->lt_ok;
     v->max_indeg = ctx->max_indeg;
     v->group_budget = ctx->group_budget;
+    v->frontier_batch = ctx->frontier_batch;
+    v->chunk_groups = ctx->chunk_groups;
+    v->queue_cap = ctx->queue_cap;
     v->big_budget = ctx->big_budget;
     v->R = v->Z = v->store_used = 0;
     v->model = -1;

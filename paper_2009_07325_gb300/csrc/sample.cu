@@ -447,10 +447,11 @@ __device__ __forceinline__ bool hash_insert(unsigned long long *ht, uint32_t epo
   return false;   // unreachable: at most kQueueCap + kCandCap < kHashSlots vertices per set
 }
 
-// Resolves the buffered live edges cand[0..ncand) of the common pass.
+// Resolves the buffered live edges cand[0..ncand) of the common pass (a
+// set that reaches qcap members is abandoned).
 __device__ __forceinline__ void common_flush(const uint32_t *__restrict__ src, const uint32_t *cand, uint32_t ncand,
                                              unsigned long long *ht, uint32_t epoch, uint32_t *q, uint32_t &tail,
-                                             bool &overflow) {
+                                             bool &overflow, uint32_t qcap) {
   const uint32_t lane = lane_id();
   const uint32_t below = (1u << lane) - 1u;
   __syncwarp();
@@ -465,10 +466,10 @@ __device__ __forceinline__ void common_flush(const uint32_t *__restrict__ src, c
     const uint32_t fm = __ballot_sync(kFullMask, fresh);
     if (fm) {
       const uint32_t pos = tail + __popc(fm & below);
-      if (fresh && pos < kQueueCap) q[pos] = u;
+      if (fresh && pos < qcap) q[pos] = u;
       tail += __popc(fm);
-      if (tail > kQueueCap) {
-        tail = kQueueCap;
+      if (tail > qcap) {
+        tail = qcap;
         overflow = true;   // the set is abandoned; its hash entries expire with the epoch
       }
     }
@@ -486,6 +487,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
   uint32_t *cand = cand_all[threadIdx.x >> 5];
   uint32_t *pe = pe_all[threadIdx.x >> 5], *pt = pt_all[threadIdx.x >> 5];
   uint32_t *q = cs.queue + (uint64_t)worker * kQueueCap;
+  const uint32_t qcap = L.queue_cap >= 32u && L.queue_cap <= kQueueCap ? L.queue_cap : kQueueCap;
   unsigned long long *ht = cs.hash + (uint64_t)worker * kHashSlots;
   uint32_t epoch = cs.epoch[worker];
 
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
       }
       head += nb;
       uint32_t ncand = 0, npend = 0;
-      auto flush = [&]() { common_flush(src, cand, ncand, ht, epoch, q, tail, overflow); };
+      auto flush = [&]() { common_flush(src, cand, ncand, ht, epoch, q, tail, overflow, qcap); };
       for (uint32_t b = 0; b < nb && !overflow; ++b) {
         const uint32_t s = __shfl_sync(kFullMask, rs, b), e = __shfl_sync(kFullMask, re, b);
         const uint32_t rt = __shfl_sync(kFullMask, rr, b);
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
           uint32_t total;
           const uint32_t excl = warp_excl(mine, total);
           if (ncand + total > kCandCap) {
-            common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
+            common_flush(src, cand, ncand, ht, epoch, q, tail, overflow, qcap);
             ncand = 0;
           }
           push_live(cand, ncand + excl, base, lv);
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
         }
       }
       if (npend) resolve_pending(pe, pt, npend, cand, ncand, kCandCap, ck, flush);
-      common_flush(src, cand, ncand, ht, epoch, q, tail, overflow);
+      common_flush(src, cand, ncand, ht, epoch, q, tail, overflow, qcap);
     }
     if (overflow) {
       if (lane == 0) defer(L, ii, j);
@@ -577,12 +579,12 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 // IC large-set pass: one block of kBigBlock threads per RR set.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kRowsPerThread = 1;       // frontier rows each thread loads per block step
-constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step
-constexpr uint32_t kChunkGroups = 512;       // groups (2048 in-edges) per chunk
-constexpr uint32_t kChunkSG = 256;           // super-groups (4096 in-edges) per chunk of a screened row
+constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step, at most
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
-static_assert(kChunkGroups % kStepGroups == 0 && kChunkSG % kStepSG == 0, "a chunk is whole warp steps");
+// A chunk is L.chunk_groups groups of 4 in-edges, or half as many
+// super-groups of 16 in a screened row; a chunk's last warp step may be
+// partial (its groups past the chunk are masked off).
 
 // Resolves a warp's buffered live edges: a source not yet in the set joins
 // the queue. Past the queue's capacity the vertex is not kept (its bit is
@@ -632,6 +634,8 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
   uint32_t *bm = bs.bitmap + (uint64_t)blockIdx.x * bs.words_per_slot;
   const uint32_t qcap = bs.q_cap;
   uint32_t *q = bs.queue + (uint64_t)blockIdx.x * qcap;
+  // the schedule's knobs (the host keeps L.batch in [32, kBatch] and L.chunk_groups >= 64)
+  const uint32_t batch = L.batch, cgroups = L.chunk_groups;
 
   for (;;) {
     // thread 0 takes the next set and plants its root (the previous set ended
@@ -667,7 +671,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
     for (;;) {
       const uint32_t tail = s_tail;
       if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
-      const uint32_t nb = tail - head < kBatch ? tail - head : kBatch;
+      const uint32_t nb = tail - head < batch ? tail - head : batch;
       uint32_t nch[kRowsPerThread], mine = 0;  // chunks of this thread's frontier rows
 #pragma unroll
       for (uint32_t r = 0; r < kRowsPerThread; ++r) {
@@ -679,9 +683,9 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
           b_s[b] = s;
           b_e[b] = e;
           b_rt[b] = rt;
-          // a chunk is kChunkGroups groups of 4 in-edges, or kChunkSG super-groups of 16
+          // a chunk is cgroups groups of 4 in-edges, or cgroups / 2 super-groups of 16
           const bool sc = screened(rt);
-          const uint32_t sh = sc ? 4u : 2u, cg = sc ? kChunkSG : kChunkGroups;
+          const uint32_t sh = sc ? 4u : 2u, cg = sc ? cgroups >> 1 : cgroups;
           nch[r] = (e > s && rt != 0u) ? (((e - 1) >> sh) - (s >> sh) + cg) / cg : 0u;
         }
         mine += nch[r];
@@ -723,15 +727,16 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
         const uint32_t s = b_s[lo], e = b_e[lo], rt = b_rt[lo], rl = lim(rt);
         if (screened(rt)) {
           const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
-          const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkSG;
-          const uint32_t c1 = c0 + kChunkSG - 1 < g1 ? c0 + kChunkSG - 1 : g1;
+          const uint32_t csg = cgroups >> 1;
+          const uint32_t c0 = g0 + (c - b_pre[lo]) * csg;
+          const uint32_t c1 = c0 + csg - 1 < g1 ? c0 + csg - 1 : g1;
           for (uint32_t base = c0; base <= c1; base += kStepSG)
             step_screened<kSGPL>(base, c1, s, e, rt, ck, pe, pt, npend, cand, ncand, kBigCand, flush);
           continue;
         }
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
-        const uint32_t c0 = g0 + (c - b_pre[lo]) * kChunkGroups;
-        const uint32_t c1 = c0 + kChunkGroups - 1 < g1 ? c0 + kChunkGroups - 1 : g1;
+        const uint32_t c0 = g0 + (c - b_pre[lo]) * cgroups;
+        const uint32_t c1 = c0 + cgroups - 1 < g1 ? c0 + cgroups - 1 : g1;
         for (uint32_t base = c0; base <= c1; base += kStepGroups) {
           uint32_t lv[kGPL];
           const uint32_t mine = step_live(thr, base, c1, s, e, rt, rl, ck, lv);
@@ -749,7 +754,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       // Resolve the buffered live edges only when the frontier runs low: while
       // at least a batch of queued vertices is still unexpanded, the next
       // batch does not need them, and the warps keep them buffered.
-      if (tail - (head + nb) < kBatch) {
+      if (tail - (head + nb) < batch) {
         if (npend) resolve_pending(pe, pt, npend, cand, ncand, kBigCand, ck, flush);
         block_flush(src, cand, ncand, bm, q, qcap, &s_tail);
         ncand = 0;

@@ -120,6 +120,9 @@ gim_status make_view(gim_server *S, gim_ctx **out) {
   c->lt_ok = S->graph->lt_ok;
   c->max_indeg = S->graph->max_indeg;
   c->group_budget = S->graph->group_budget;
+  c->frontier_batch = S->graph->frontier_batch;
+  c->chunk_groups = S->graph->chunk_groups;
+  c->queue_cap = S->graph->queue_cap;
   *out = c;
   return GIM_OK;
 }

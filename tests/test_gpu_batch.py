@@ -81,14 +81,21 @@ def test_batch_twice_in_a_row_and_errors():
 
 
 def test_schedule_never_changes_results():
-    """The group budget (warps per heavy RR set) changes speed only."""
+    """Every schedule knob changes speed only: the group budget (warps per
+    heavy RR set), the block pass's chunk and frontier batch, the warp
+    pass's queue capacity."""
     g = I.wc_weights(I.rmat(16, 8))
     ref = None
-    for budget in (1, 64, 4096, 1 << 30):
+    schedules = [dict(group_budget=b) for b in (1, 64, 4096, 1 << 30)]
+    schedules += [dict(group_budget=64, chunk_groups=cg, frontier_batch=fb)
+                  for cg, fb in ((64, 32), (256, 96), (4096, 256), (1024, 64))]
+    schedules += [dict(group_budget=1 << 30, queue_cap=qc) for qc in (256, 1024)]
+    for sched in schedules:
         c = Context(0)
         c.load(g)
-        c.set_option(binding.GIM_OPT_GROUP_BUDGET, budget)
-        assert c.get_option(binding.GIM_OPT_GROUP_BUDGET) == budget
+        for name, value in sched.items():
+            c.set_option(binding.SCHEDULE_OPTIONS[name], value)
+        assert {k: c.schedule()[k] for k in sched} == sched
         c.sample_rr(GIM_IC, 8000, 5)
         got = c.rr_export(), c.coverage(), c.select_seeds(20)
         if ref is None:
@@ -98,6 +105,20 @@ def test_schedule_never_changes_results():
             assert np.array_equal(got[1], ref[1])
             assert [x.tolist() if hasattr(x, "tolist") else x for x in got[2]] == \
                    [x.tolist() if hasattr(x, "tolist") else x for x in ref[2]]
+
+
+def test_schedule_options_reject_values_out_of_range():
+    c = Context(0)
+    c.load(I.wc_weights(I.er(200, 1000, 3)))
+    for opt, bad in ((binding.GIM_OPT_FRONTIER_BATCH, 16), (binding.GIM_OPT_FRONTIER_BATCH, 257),
+                     (binding.GIM_OPT_FRONTIER_BATCH, 100), (binding.GIM_OPT_CHUNK_GROUPS, 32),
+                     (binding.GIM_OPT_CHUNK_GROUPS, 100), (binding.GIM_OPT_CHUNK_GROUPS, 8192),
+                     (binding.GIM_OPT_QUEUE_CAP, 128), (binding.GIM_OPT_QUEUE_CAP, 8192),
+                     (binding.GIM_OPT_QUEUE_CAP, 1000)):
+        before = c.get_option(opt)
+        with pytest.raises(GimError):
+            c.set_option(opt, bad)
+        assert c.get_option(opt) == before
 
 
 def test_autotune_picks_a_candidate_and_caches_it():
@@ -110,6 +131,9 @@ def test_autotune_picks_a_candidate_and_caches_it():
     b2, m2 = binding.autotune(cs, params, 500)
     assert b1 in (1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 30) and m1 and b1 == b2 and not m2
     assert all(c.get_option(binding.GIM_OPT_GROUP_BUDGET) == b1 and c.rr_count() == (0, 0) for c in cs)
+    sched = cs[0].schedule()
+    assert sched["chunk_groups"] in (256, 512, 1024, 2048) and sched["frontier_batch"] in (64, 128, 256)
+    assert sched["queue_cap"] in (1024, 2048, 4096) and all(c.schedule() == sched for c in cs)
     r = binding.batch_imm(cs, params)
     for c, p, x in zip(cs, params, r):
         alone = Context(0)
