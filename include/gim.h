@@ -349,12 +349,27 @@ typedef enum {
   /* Members an RR set may reach in the warp-per-set IC pass before it is
      handed to the block-per-set pass (the warp's queue): 256 .. 4096, a
      multiple of 32. Default 4096. */
-  GIM_OPT_QUEUE_CAP = 5
+  GIM_OPT_QUEUE_CAP = 5,
+  /* 1: compact collections for gim_imm (T = 1, IC or LT). The greedy's first
+     pick (the vertex in the most RR sets, lowest id on ties; Alg. 1) covers
+     every set that holds it, so the later rounds never read those sets'
+     members. After its first selection gim_imm keeps, for every set it draws
+     from then on that holds that first pick, only the set's size and its
+     occurrence counts, not its members. Where one vertex lies in nearly all
+     of the large sets (IC with a giant component, e.g. p = 0.01 on R-MAT)
+     this shrinks the collection by orders of magnitude. Results are those of
+     the plain run: each later selection checks on the device that its first
+     pick is still that vertex and fails with GIM_ERR_STATE otherwise (never a
+     different answer). A sampling call that fails empties a compact
+     collection instead of rolling it back. gim_rr_export then fails on such
+     sets (gim_rr_export_compact, gim_rr_info read them). gim_batch_imm, the
+     server and multi-round IM ignore it. 0 (default): every set is kept. */
+  GIM_OPT_COMPACT_FIRST_PICK = 6
 } gim_option;
 
 /* Sets an option. Errors: GIM_ERR_ARG (unknown option, value 0 for the
    tuning knobs or outside a knob's stated range, value above 1 for
-   GIM_OPT_FRESH_FINAL). */
+   GIM_OPT_FRESH_FINAL or GIM_OPT_COMPACT_FIRST_PICK). */
 gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value);
 
 /* Reads a tuning knob into *value. */
@@ -384,20 +399,35 @@ gim_status gim_autotune(gim_ctx *const *ctxs, uint32_t n_inst, const gim_imm_par
 
 /* ---- introspection (tests, tools) ------------------------------------- */
 
-/* *count_out = |R|; *members_out (nullable) = total members over all sets. */
+/* *count_out = |R|; *members_out (nullable) = total members over all sets
+   whose members are kept (a compact collection's sets that hold the compact
+   vertex count none: see GIM_OPT_COMPACT_FIRST_PICK). */
 gim_status gim_rr_count(gim_ctx *ctx, uint64_t *count_out, uint64_t *members_out);
 
 /*
  * Copies R out in rr_id order as a CSR: offsets_out has |R|+1 entries,
  * members_out has gim_rr_count's members_out entries; the members of each
- * set are written in ascending vertex order.
+ * set are written in ascending vertex order. GIM_ERR_STATE if a set is kept
+ * without its members (compact collections: use gim_rr_export_compact).
  */
 gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out);
 
 /*
+ * As gim_rr_export, for a compact collection: a set kept without its members
+ * (it holds the compact vertex) is exported with none, and compact_out[j]
+ * (|R| bytes) is 1 for it, 0 for every other set. Its size: gim_rr_info.
+ */
+gim_status gim_rr_export_compact(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out, uint8_t *compact_out);
+
+/* Size of RR set rr_id (rr_id < |R|) and *stored_out = 1 if its members are
+   kept, 0 if it is a compact collection's set that holds the compact vertex. */
+gim_status gim_rr_info(gim_ctx *ctx, uint64_t rr_id, uint32_t *len_out, int *stored_out);
+
+/*
  * Copies RR set rr_id (rr_id < |R|) in ascending vertex order into
  * members_out (cap entries) and its size into *len_out. A set larger than cap
- * gives GIM_ERR_ARG with *len_out set, so a caller can retry with room.
+ * gives GIM_ERR_ARG with *len_out set, so a caller can retry with room; a set
+ * kept without its members (compact collections) gives GIM_ERR_STATE.
  */
 gim_status gim_rr_get(gim_ctx *ctx, uint64_t rr_id, uint32_t *members_out, uint32_t cap, uint32_t *len_out);
 

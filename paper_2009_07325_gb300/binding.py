@@ -23,6 +23,7 @@ GIM_OPT_FRESH_FINAL = 2
 GIM_OPT_FRONTIER_BATCH = 3
 GIM_OPT_CHUNK_GROUPS = 4
 GIM_OPT_QUEUE_CAP = 5
+GIM_OPT_COMPACT_FIRST_PICK = 6
 SCHEDULE_OPTIONS = {"group_budget": GIM_OPT_GROUP_BUDGET, "chunk_groups": GIM_OPT_CHUNK_GROUPS,
                     "frontier_batch": GIM_OPT_FRONTIER_BATCH, "queue_cap": GIM_OPT_QUEUE_CAP}
 STATUS = {0: "GIM_OK", 1: "GIM_ERR_ARG", 2: "GIM_ERR_OOM", 3: "GIM_ERR_CUDA", 4: "GIM_ERR_TIMEOUT",
@@ -77,6 +78,8 @@ SIGNATURES = {
     "gim_server_stop": (None, [_vp]),
     "gim_rr_count": (ctypes.c_int, [_vp, _c_u64p, _c_u64p]),
     "gim_rr_export": (ctypes.c_int, [_vp, _c_u64p, _c_u32p]),
+    "gim_rr_export_compact": (ctypes.c_int, [_vp, _c_u64p, _c_u32p, ctypes.POINTER(ctypes.c_uint8)]),
+    "gim_rr_info": (ctypes.c_int, [_vp, ctypes.c_uint64, _c_u32p, ctypes.POINTER(ctypes.c_int)]),
     "gim_coverage_export": (ctypes.c_int, [_vp, _c_u32p]),
     "gim_last_timings": (ctypes.c_int, [_vp, _c_f64p]),
     "gim_reset_timings": (ctypes.c_int, [_vp]),
@@ -230,6 +233,25 @@ class Context:
         mem = np.zeros(max(Z, 1), np.uint32)
         self._check(self.L.gim_rr_export(self.h, _p(off, _c_u64p), _p(mem, _c_u32p)), "gim_rr_export")
         return off, mem[:Z]
+
+    def rr_export_compact(self):
+        """(offsets, members, compact): a compact collection as a CSR; the sets
+        kept without members export none and have compact[j] = 1."""
+        R, Z = self.rr_count()
+        off = np.zeros(R + 1, np.uint64)
+        mem = np.zeros(max(Z, 1), np.uint32)
+        flags = np.zeros(max(R, 1), np.uint8)
+        self._check(self.L.gim_rr_export_compact(self.h, _p(off, _c_u64p), _p(mem, _c_u32p),
+                                                 flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+                    "gim_rr_export_compact")
+        return off, mem[:Z], flags[:R]
+
+    def rr_info(self, rr_id: int):
+        """(size, stored) of RR set rr_id."""
+        n = ctypes.c_uint32(0)
+        stored = ctypes.c_int(0)
+        self._check(self.L.gim_rr_info(self.h, rr_id, ctypes.byref(n), ctypes.byref(stored)), "gim_rr_info")
+        return int(n.value), bool(stored.value)
 
     def coverage(self) -> np.ndarray:
         """Occurrence counts: n entries, or T*n for a multi-round collection."""

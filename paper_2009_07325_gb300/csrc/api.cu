@@ -108,6 +108,7 @@ gim_status do_select(gim_ctx *ctx, uint32_t k, uint32_t *seeds_out, uint64_t *co
   x.cnt = ctx->st.cnt;
   x.buf = &ctx->sel;
   x.k = picks;
+  x.skip = ctx->skip_vertex;
   if (T > 1) {
     x.part_n = ctx->g.n;
     x.part_k = k;
@@ -173,6 +174,10 @@ gim_status run_imm(gim_ctx *ctx, gim_model model, uint32_t T, uint32_t k, double
     if ((st = sample_to(theta_i)) != GIM_OK) return st;
     uint64_t cov = 0;
     if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, &cov, nullptr); })) != GIM_OK) return st;
+    // compact collection: the sets drawn from now on that hold the first pick
+    // keep only their size (every later selection checks that its first pick
+    // is still this vertex, and fails otherwise)
+    if (ctx->compact && T == 1 && ctx->skip_vertex == kNoSkip) ctx->skip_vertex = seeds_out[0];
     ++rounds;
     const double est = ((double)n * (double)cov) / (double)ctx->R;
     if (est >= (1.0 + c.epsp) * x) {
@@ -182,8 +187,10 @@ gim_status run_imm(gim_ctx *ctx, gim_model model, uint32_t T, uint32_t k, double
   }
   const uint64_t theta = (uint64_t)std::ceil(c.lam2 / LB);
   if (ctx->fresh_final && T == 1) {   // theta new sets, rr_ids 2^63 + j, replace the search's collection
+    const uint32_t skip = ctx->skip_vertex;   // a compact collection stays compact
     if ((st = gim_reset_rr(ctx)) != GIM_OK) return st;
     ctx->jhi = ctx->rhi = 1u << 31;
+    ctx->skip_vertex = skip;
   }
   if ((st = sample_to(theta)) != GIM_OK) return st;
   if ((st = timed(t_select, [&] { return do_select(ctx, k, seeds_out, nullptr, nullptr); })) != GIM_OK) return st;
@@ -352,6 +359,7 @@ gim_status gim_graph_load(gim_ctx *ctx, uint32_t n, uint64_t m, const uint64_t *
   ctx->model = -1;
   ctx->jhi = ctx->rhi = 0;
   ctx->rounds = 1;
+  ctx->skip_vertex = kNoSkip;
   if (ctx->cnt_cap < (uint64_t)n + 4) {
     dfree(ctx->st.cnt);
     ctx->cnt_cap = 0;
@@ -407,6 +415,7 @@ gim_status gim_reset_rr(gim_ctx *ctx) {
   ctx->R = ctx->Z = ctx->store_used = 0;
   ctx->model = -1;
   ctx->jhi = ctx->rhi = 0;
+  ctx->skip_vertex = kNoSkip;
   CU(cudaMemsetAsync(ctx->st.cnt, 0, (uint64_t)ctx->g.n * ctx->rounds * 4, ctx->stream));
   ctx->rounds = 1;
   CU(cudaStreamSynchronize(ctx->stream));
@@ -513,6 +522,10 @@ gim_status gim_set_option(gim_ctx *ctx, gim_option opt, uint64_t value) {
     ctx->fresh_final = value == 1;
     return GIM_OK;
   }
+  if (opt == GIM_OPT_COMPACT_FIRST_PICK && value <= 1) {
+    ctx->compact = value == 1;
+    return GIM_OK;
+  }
   if (opt == GIM_OPT_FRONTIER_BATCH && value >= 32 && value <= 256 && value % 32 == 0) {
     ctx->frontier_batch = (uint32_t)value;
     return GIM_OK;
@@ -536,6 +549,10 @@ gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value) {
   }
   if (opt == GIM_OPT_LARGE_PASS_BYTES) {
     *value = ctx->big_budget;
+    return GIM_OK;
+  }
+  if (opt == GIM_OPT_COMPACT_FIRST_PICK) {
+    *value = ctx->compact ? 1 : 0;
     return GIM_OK;
   }
   if (opt == GIM_OPT_FRONTIER_BATCH) {
@@ -590,6 +607,9 @@ gim_status gim_rr_get(gim_ctx *ctx, uint64_t rr_id, uint32_t *members_out, uint3
   CU(cudaMemcpyAsync(&start, ctx->st.rr_start + rr_id, 8, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaMemcpyAsync(&len, ctx->st.rr_len + rr_id, 4, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
+  if (start == kSkipped)
+    return set_err(ctx, GIM_ERR_STATE, "RR set %llu holds the compact vertex: only its size is kept (gim_rr_info)",
+                   (unsigned long long)rr_id);
   if (start == kNoStart || start + len > ctx->store_used)
     return set_err(ctx, GIM_ERR_STATE, "RR set %llu is not stored", (unsigned long long)rr_id);
   *len_out = len;
@@ -602,7 +622,11 @@ gim_status gim_rr_get(gim_ctx *ctx, uint64_t rr_id, uint32_t *members_out, uint3
   return GIM_OK;
 }
 
-gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out) {
+namespace {
+// The collection as a CSR in rr_id order (members ascending within a set). A
+// set stored without members (compact) exports none and sets its flag, or
+// fails the export when compact_out is null.
+gim_status export_impl(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out, uint8_t *compact_out) {
   gim_status st = check_ctx(ctx);
   if (st) return st;
   if (!offsets_out || (ctx->Z > 0 && !members_out)) return set_err(ctx, GIM_ERR_ARG, "null output");
@@ -620,12 +644,45 @@ gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_
   offsets_out[0] = 0;
   for (uint64_t j = 0; j < R; ++j) {
     const uint64_t o = offsets_out[j];
+    if (start[j] == kSkipped) {
+      if (!compact_out)
+        return set_err(ctx, GIM_ERR_STATE, "RR set %llu holds the compact vertex: only its size is kept",
+                       (unsigned long long)j);
+      compact_out[j] = 1;
+      offsets_out[j + 1] = o;
+      continue;
+    }
     if (start[j] == kNoStart || start[j] + len[j] > ctx->store_used)
       return set_err(ctx, GIM_ERR_STATE, "RR set %llu is not stored", (unsigned long long)j);
+    if (compact_out) compact_out[j] = 0;
     std::memcpy(members_out + o, store.data() + start[j], (size_t)len[j] * 4);
     std::sort(members_out + o, members_out + o + len[j]);
     offsets_out[j + 1] = o + len[j];
   }
+  return GIM_OK;
+}
+}  // namespace
+
+gim_status gim_rr_export(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out) {
+  return export_impl(ctx, offsets_out, members_out, nullptr);
+}
+
+gim_status gim_rr_export_compact(gim_ctx *ctx, uint64_t *offsets_out, uint32_t *members_out, uint8_t *compact_out) {
+  if (!compact_out) return ctx ? set_err(ctx, GIM_ERR_ARG, "compact_out is null") : GIM_ERR_ARG;
+  return export_impl(ctx, offsets_out, members_out, compact_out);
+}
+
+gim_status gim_rr_info(gim_ctx *ctx, uint64_t rr_id, uint32_t *len_out, int *stored_out) {
+  gim_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!len_out || !stored_out) return set_err(ctx, GIM_ERR_ARG, "null output");
+  if (rr_id >= ctx->R) return set_err(ctx, GIM_ERR_ARG, "rr_id %llu >= |R|", (unsigned long long)rr_id);
+  uint64_t start = 0;
+  CU(cudaMemcpyAsync(&start, ctx->st.rr_start + rr_id, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(len_out, ctx->st.rr_len + rr_id, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (start == kNoStart) return set_err(ctx, GIM_ERR_STATE, "RR set %llu is not stored", (unsigned long long)rr_id);
+  *stored_out = start == kSkipped ? 0 : 1;
   return GIM_OK;
 }
 

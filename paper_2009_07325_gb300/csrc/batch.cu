@@ -54,7 +54,8 @@ struct SelDesc {
   uint8_t *hslot;                         // n: hub slot or 0xFF
   uint32_t *hbits;                        // hub rows of `words` words
   uint32_t *hmeta;                        // hub count, ids, counts + 1
-  unsigned int *err;                      // bit 1: more hubs than kHeavyCap (cannot happen: see hub_min)
+  unsigned int *err;                      // bit 2: more hubs than kHeavyCap (cannot happen: see hub_min);
+                                          // bit 4: a set stored without members where its members are needed
   uint32_t ext;                           // 1: lists, hub split and rows come from another instance's index
   const uint32_t *ext_hmeta;              // that index's hub count and ids
   unsigned long long *best;               // k argmax keys
@@ -70,6 +71,17 @@ struct SelDesc {
   // marked covered by the fill and left out of the index, and the light
   // counts are the lengths of the lists filled (bsel_first_*)
   uint32_t fuse;
+  // a compact collection's vertex: its sets are stored without members
+  // (rr_start = kSkipped); they are covered by a first pick equal to it, and
+  // any other use of them is an error (bit 4 of err)
+  uint32_t skip;
+  // 1 (a fused instance whose collection holds such sets): the first pick is
+  // taken from cnt before anything else (bsel_pick), its sets are marked
+  // covered (bsel_detect), and the inverted lists are laid out by `lay`, the
+  // counts over the uncovered stored sets only (bsel_count_open), since cnt
+  // also counts members that are not stored
+  uint32_t compact;
+  uint32_t *lay;                          // layout counts: cnt, or the slot's own counts when compact
 };
 
 // Instance of block b: the last i with begin(i) <= b.
@@ -142,8 +154,10 @@ __global__ void __launch_bounds__(kSelThreads) bsel_clear(const SelDesc *d, uint
 __global__ void __launch_bounds__(kSelThreads) bsel_cnt_clear(const SelDesc *d, uint32_t ni) {
   for (uint32_t i = blockIdx.y; i < ni; i += gridDim.y) {
     const SelDesc &D = d[i];
-    if (!D.active || !D.count_own || D.count_from != 0) continue;
-    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < D.n; x += gridDim.x * blockDim.x) D.cnt[x] = 0u;
+    if (!D.active) continue;
+    uint32_t *c = D.compact ? D.lay : (D.count_own && D.count_from == 0) ? D.cnt : nullptr;
+    if (!c) continue;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < D.n; x += gridDim.x * blockDim.x) c[x] = 0u;
   }
 }
 
@@ -162,6 +176,10 @@ __global__ void __launch_bounds__(kSelThreads) bsel_count(const SelDesc *d, uint
     const SelDesc &D = d[i];
     const uint64_t j = D.count_from + (g - D.cnt_begin);
     const uint64_t b = D.rr_start[j];
+    if (b == kSkipped) {
+      if (lane == 0) atomicOr(D.err, 4u);
+      continue;
+    }
     const uint32_t len = D.rr_len[j];
     for (uint32_t t = lane; t < len; t += 32) atomicAdd(&D.cnt[D.members[b + t]], 1u);
   }
@@ -179,8 +197,8 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_sums(const SelDesc *d, 
   for (uint32_t t = 0; t < kTileItems; ++t) {
     const uint64_t x = base + (uint64_t)t * kSelThreads;
     if (x < D.n) {
-      const uint32_t c = D.cnt[x];
-      s += c < D.hub_min ? c : 0u;        // hubs have no inverted list
+      const uint32_t c = D.cnt[x], l = D.lay[x];
+      s += l < D.hub_min ? l : 0u;        // hubs have no inverted list
       // the greedy's key (count + 1) << 32 | ~id: the largest is the first pick (lowest id on ties)
       const unsigned long long kx = ((unsigned long long)(c + 1u) << 32) | (uint32_t)~(uint32_t)x;
       key = kx > key ? kx : key;
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_tile_sums(const SelDesc *d, 
   unsigned long long ex;
   const unsigned long long tot = block_excl(s, &ex);
   if (threadIdx.x == 0) D.tile_sum[blockIdx.x - D.tile_begin] = tot;
-  if (D.fuse) {   // one atomic per block
+  if (D.fuse && !D.compact) {   // one atomic per block (a compact instance took it in bsel_pick)
     __shared__ unsigned long long wk[kSelThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -237,7 +255,7 @@ __global__ void __launch_bounds__(kSelThreads) bsel_apply(const SelDesc *d, uint
     const uint64_t row0 = (uint64_t)tile * kTile + (uint64_t)r * kSelThreads;
     if (row0 >= D.n) break;                  // block-uniform
     const uint64_t x = row0 + threadIdx.x;
-    const uint32_t v = x < D.n ? D.cnt[x] : 0u;
+    const uint32_t v = x < D.n ? D.lay[x] : 0u;
     const bool hub = v >= D.hub_min;
     const uint32_t light = hub ? 0u : v;
     unsigned long long ex;
@@ -335,19 +353,29 @@ __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint3
     const bool valid = jl < D.fill_R;
     const uint64_t b = valid ? D.rr_start[jl] : 0ull;
     const uint32_t len = valid ? D.rr_len[jl] : 0u;
-    uint32_t incl = len;
+    const bool compact = valid && b == kSkipped;   // stored without members: holds D.skip
+    // a compact instance's sets that hold the first pick are marked already (bsel_detect)
+    const bool covd = D.compact && valid && ((__ldcg(D.covered + (jl >> 5)) >> (jl & 31u)) & 1u);
+    const uint32_t walk = (compact || covd) ? 0u : len;   // members this set contributes to the walk
+    uint32_t incl = walk;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
       if (lane >= (uint32_t)o) incl += t;
     }
     const uint32_t T = __shfl_sync(kFullMask, incl, 31);   // members of the 32 sets
-    const uint32_t pre = incl - len;
+    const uint32_t pre = incl - walk;
     const bool hubs = D.hmeta[0] != 0u;
     uint32_t skip = 0;   // bit s: set j0 + s is covered by the first pick
-    if (D.fuse) {
+    const uint32_t cmask = __ballot_sync(kFullMask, compact);
+    if (cmask && !D.compact && (!D.fuse || ~(uint32_t)*D.best != D.skip)) {
+      // a compact set's members are needed (a selection without the fused first
+      // pick, or a first pick other than the compact vertex): the selection fails
+      if (lane == 0) atomicOr(D.err, 4u);
+    }
+    if (D.fuse && !D.compact) {
       const uint32_t u1 = ~(uint32_t)*D.best;
-      uint32_t hit = 0;
+      uint32_t hit = cmask;   // a compact set holds D.skip, which is the first pick here
       for (uint32_t p0 = 0; p0 < T; p0 += 128) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -391,6 +419,133 @@ __global__ void __launch_bounds__(kSelThreads) bsel_fill(const SelDesc *d, uint3
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (x[q] != 0xFFFFFFFFu && hs[q] == 0xFFu) D.inv[pos[q]] = jq[q];
+    }
+  }
+}
+
+// Compact collections, step 1 (before the tile sums): the first pick, the
+// largest key (count + 1) << 32 | ~id over the occurrence counts, into
+// best[0] (one block per tile, like bsel_tile_sums).
+__global__ void __launch_bounds__(kSelThreads) bsel_pick(const SelDesc *d, uint32_t ni) {
+  const uint32_t i = owner(d, ni, blockIdx.x, [](const SelDesc &x) { return (uint64_t)x.tile_begin; });
+  const SelDesc &D = d[i];
+  if (!D.active || !D.compact) return;
+  const uint64_t base = (uint64_t)(blockIdx.x - D.tile_begin) * kTile + threadIdx.x;
+  unsigned long long key = 0;
+#pragma unroll 4
+  for (uint32_t t = 0; t < kTileItems; ++t) {
+    const uint64_t x = base + (uint64_t)t * kSelThreads;
+    if (x < D.n) {
+      const unsigned long long kx = ((unsigned long long)(D.cnt[x] + 1u) << 32) | (uint32_t)~(uint32_t)x;
+      key = kx > key ? kx : key;
+    }
+  }
+  __shared__ unsigned long long wk[kSelThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(kFullMask, key, o);
+    key = y > key ? y : key;
+  }
+  if ((threadIdx.x & 31u) == 0) wk[threadIdx.x >> 5] = key;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kSelThreads / 32; ++w) key = wk[w] > key ? wk[w] : key;
+    atomicMax(D.best, key);
+  }
+}
+
+// A warp's group of 32 consecutive sets [j0, j0 + 32) of a compact
+// instance, walked as one list of the members that are stored (lane s holds
+// set j0 + s): sizes, starts, exclusive prefix of the stored sizes.
+struct Group32 {
+  uint64_t jl, b;
+  uint32_t len, walk, pre, T;
+  bool valid, compact;
+};
+
+__device__ __forceinline__ Group32 group32(const SelDesc &D, uint64_t j0, bool skip_covered) {
+  const uint32_t lane = threadIdx.x & 31u;
+  Group32 G;
+  G.jl = j0 + lane;
+  G.valid = G.jl < D.fill_R;
+  G.b = G.valid ? D.rr_start[G.jl] : 0ull;
+  G.len = G.valid ? D.rr_len[G.jl] : 0u;
+  G.compact = G.valid && G.b == kSkipped;
+  const bool covd = skip_covered && G.valid && ((__ldcg(D.covered + (G.jl >> 5)) >> (G.jl & 31u)) & 1u);
+  G.walk = (G.compact || covd) ? 0u : G.len;
+  uint32_t incl = G.walk;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= (uint32_t)o) incl += t;
+  }
+  G.T = __shfl_sync(kFullMask, incl, 31);
+  G.pre = incl - G.walk;
+  return G;
+}
+
+// The stored member at walk position p (< G.T) of a group: warp-wide.
+__device__ __forceinline__ uint32_t group_member(const SelDesc &D, const Group32 &G, uint32_t p, uint32_t &s) {
+  s = set_of(G.pre, p);
+  const uint64_t bs = ((uint64_t)__shfl_sync(kFullMask, (uint32_t)(G.b >> 32), s) << 32) |
+                      __shfl_sync(kFullMask, (uint32_t)G.b, s);
+  const uint32_t ps = __shfl_sync(kFullMask, G.pre, s);
+  return p < G.T ? D.members[bs + (p - ps)] : 0xFFFFFFFFu;
+}
+
+// Compact collections, step 2: every set that holds the first pick is
+// covered in round 0 - a set kept without members holds the compact vertex,
+// which must be the first pick (else bit 4 of err), a stored set is scanned.
+// Marks them covered and counts their members for the statistics.
+__global__ void __launch_bounds__(kSelThreads) bsel_detect(const SelDesc *d, uint32_t ni) {
+  const unsigned long long total = d[ni - 1].grp_begin + (d[ni - 1].fill_R + 31) / 32;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t g = warp; g < total; g += nwarps) {
+    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.grp_begin; });
+    const SelDesc &D = d[i];
+    if (!D.compact) continue;
+    const Group32 G = group32(D, (g - D.grp_begin) * 32, false);
+    const uint32_t u1 = ~(uint32_t)*D.best;
+    const uint32_t cmask = __ballot_sync(kFullMask, G.compact);
+    if (cmask && u1 != D.skip && lane == 0) atomicOr(D.err, 4u);
+    uint32_t hit = cmask;
+    for (uint32_t p0 = 0; p0 < G.T; p0 += 128) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t s;
+        const uint32_t x = group_member(D, G, p0 + 32 * q + lane, s);
+        if (x == u1) hit |= 1u << s;
+      }
+    }
+    hit = __reduce_or_sync(kFullMask, hit);
+    if ((hit >> lane) & 1u) {
+      atomicOr(D.covered + (G.jl >> 5), 1u << (G.jl & 31u));
+      atomicAdd(D.stats, (unsigned long long)G.len);
+    }
+  }
+}
+
+// Compact collections, step 3: the layout counts, over the stored sets left
+// uncovered.
+__global__ void __launch_bounds__(kSelThreads) bsel_count_open(const SelDesc *d, uint32_t ni) {
+  const unsigned long long total = d[ni - 1].grp_begin + (d[ni - 1].fill_R + 31) / 32;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t g = warp; g < total; g += nwarps) {
+    const uint32_t i = owner(d, ni, g, [](const SelDesc &x) { return (uint64_t)x.grp_begin; });
+    const SelDesc &D = d[i];
+    if (!D.compact) continue;
+    const Group32 G = group32(D, (g - D.grp_begin) * 32, true);
+    for (uint32_t p0 = 0; p0 < G.T; p0 += 128) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t s;
+        const uint32_t x = group_member(D, G, p0 + 32 * q + lane, s);
+        if (x != 0xFFFFFFFFu) atomicAdd(D.lay + x, 1u);
+      }
     }
   }
 }
@@ -472,6 +627,9 @@ cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uin
   bsel_clear<<<dim3(64, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_cnt_clear<<<dim3(cnt_blocks, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_count<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_pick<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_detect<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  bsel_count_open<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
   bsel_tile_sums<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
   bsel_tile_scan<<<ni, kSelThreads, 0, s>>>(d, ni);
   bsel_apply<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
@@ -648,20 +806,23 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     // the first pick rides on the fill for an instance that indexes its own
     // collection for itself (not a shared index, not multi-round)
     D.fuse = (D.active && !D.ext && !x.index_only && x.part_n == 0 && D.k >= 1) ? 1u : 0u;
+    D.skip = x.skip;
+    D.compact = (D.fuse && x.skip != kNoSkip && x.cnt) ? 1u : 0u;
     if (!D.active) continue;
     total_sets += (D.fill_R + 31) / 32;
     SelectBuffers &b = *x.buf;
     const uint32_t *own_before = b.cnt_own;
+    const bool need_own = !x.cnt || D.compact;   // own counts, or a compact instance's layout counts
     if (b.n_cap < (uint64_t)D.n + 4 || !b.cnt_work || !b.inv_off || !b.cursor || !b.hslot ||
-        (!x.cnt && !b.cnt_own)) {   // the n-sized buffers share n_cap
+        (need_own && !b.cnt_own)) {   // the n-sized buffers share n_cap
       uint64_t c0 = b.n_cap, c1 = b.n_cap, c2 = b.n_cap, c3 = b.n_cap, c4 = b.n_cap;
       CU(ensure_buf(b.cnt_work, c0, (uint64_t)D.n + 4));
       CU(ensure_buf(b.inv_off, c1, (uint64_t)D.n + 4));
       CU(ensure_buf(b.cursor, c2, (uint64_t)D.n + 4));
       CU(ensure_buf(b.hslot, c4, (uint64_t)D.n + 4));
-      if (!x.cnt) CU(ensure_buf(b.cnt_own, c3, (uint64_t)D.n + 4));
+      if (need_own) CU(ensure_buf(b.cnt_own, c3, (uint64_t)D.n + 4));
       b.n_cap = std::min(std::min(c0, c4), std::min(c1, c2));
-      if (!x.cnt) b.n_cap = std::min(b.n_cap, c3);
+      if (need_own) b.n_cap = std::min(b.n_cap, c3);
     }
     // A hub is a vertex in at least hub_min sets: at least R/32 (its bitmap
     // row is no longer than its inverted list would be) and at least
@@ -689,6 +850,7 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
     D.rr_len = x.rr_len;
     D.count_own = x.cnt ? 0u : 1u;
     D.cnt = x.cnt ? const_cast<uint32_t *>(x.cnt) : b.cnt_own;
+    D.lay = D.compact ? b.cnt_own : D.cnt;
     if (!x.cnt) {
       // counts carried over from the slot's previous round survive only in the same buffer
       const bool keep = b.cnt_own == own_before && x.count_from <= x.R;
@@ -772,7 +934,7 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
   }
   CU(cudaEventRecord(ctx->ev[8], s));
   CU(cudaGraphLaunch(B.exec, s));
-  ctx->launches += 11;
+  ctx->launches += 14;
   for (size_t w = 0; w < B.wave_first.size(); ++w) {
     const uint32_t first = B.wave_first[w];
     const uint32_t count = (w + 1 < B.wave_first.size() ? B.wave_first[w + 1] : B.ni) - first;
@@ -793,6 +955,10 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
   CU(cudaMemcpyAsync(&flags, B.sync + B.ni, sizeof flags, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   if (flags & 2u) return set_err(ctx, GIM_ERR_STATE, "greedy selection: more hubs than slots");
+  if (flags & 4u)
+    return set_err(ctx, GIM_ERR_STATE,
+                   "selection: the collection keeps some sets without members (compact), and this selection "
+                   "needs them: its first pick is not the compact vertex");
   if (flags) return set_err(ctx, GIM_ERR_TIMEOUT, "greedy selection: a block barrier wait gave up");
   // device time and algorithmic bytes: reading the store and writing the
   // index (8 per member) and scanning the counts (4 per vertex); then per
@@ -828,6 +994,7 @@ gim_status batch_imm(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *pa
     c->model = -1;
     c->jhi = c->rhi = 0;
     c->rounds = 1;
+    c->skip_vertex = kNoSkip;   // the batch keeps every set
     CU(cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * 4, s));
     imm_init(S[i], c->g.n, params[i]);
     ns[i] = c->g.n;

@@ -280,6 +280,7 @@ void fill_desc(InstDesc &d, gim_ctx *c, uint64_t seed, uint64_t item_begin) {
   d.rhi = c->rhi;
   d.moff = c->moff;
   d.idoff = c->idoff;
+  d.skip = c->skip_vertex;
   d.item_begin = item_begin;
   d.store_tail = c->store_used;
   d.members_added = 0;
@@ -418,8 +419,18 @@ gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s) {
       launch_uncount(u, s);
       cudaStreamSynchronize(s);
       for (uint32_t i = 0; i < grp.size(); ++i) {
-        grp[i]->ctx->Z = Z0[i];
-        grp[i]->ctx->store_used = used0[i];
+        gim_ctx *c = grp[i]->ctx;
+        c->Z = Z0[i];
+        c->store_used = used0[i];
+        if (c->skip_vertex != kNoSkip) {
+          // the counts of sets stored without members cannot be lowered again:
+          // a compact collection is emptied instead of rolled back
+          c->R = c->Z = c->store_used = 0;
+          c->model = -1;
+          c->skip_vertex = kNoSkip;
+          cudaMemsetAsync(c->st.cnt, 0, (uint64_t)c->g.n * c->rounds * 4, s);
+          cudaStreamSynchronize(s);
+        }
       }
     };
     unsigned long long *list_a = D.d_def, *list_b = D.d_def + D.def_cap / 2;

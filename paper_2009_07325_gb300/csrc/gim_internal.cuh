@@ -15,6 +15,8 @@ namespace gim {
 
 constexpr uint32_t kFullMask = 0xFFFFFFFFu;
 constexpr uint64_t kNoStart = ~0ull;          // rr_start of a set not (yet) stored
+constexpr uint64_t kSkipped = ~0ull - 1;      // rr_start of a set holding the skipped vertex: counted, members not kept
+constexpr uint32_t kNoSkip = 0xFFFFFFFFu;     // no skipped vertex
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). Counter words are
@@ -186,7 +188,7 @@ struct InstDesc {
   uint32_t rhi;
   uint32_t moff;
   uint32_t idoff;
-  uint32_t pad1;
+  uint32_t skip;   // a set holding this vertex keeps only its size (rr_start = kSkipped); kNoSkip: none
   // written by the kernels
   unsigned long long store_tail;     // store entries reserved (starts at the entries already used)
   unsigned long long members_added;  // members of the sets stored by this launch
@@ -200,7 +202,7 @@ struct SampleCtl {
   unsigned int pad;
 };
 
-enum : unsigned int { kErrDeferredFull = 1u };
+enum : unsigned int { kErrDeferredFull = 1u, kErrUncountSkipped = 2u };
 
 // A sampling launch: the instances, the work items and where to defer.
 struct SampleLaunch {
@@ -454,6 +456,7 @@ struct SelInput {
   uint64_t index_R = 0;
   bool index_only = false;               // build this instance's index only (no greedy rounds)
   uint32_t part_n = 0, part_k = 0;       // multi-round partition (see GreedyDesc)
+  uint32_t skip = kNoSkip;               // sets [0, R) holding this vertex may be stored without members
 };
 
 // Greedy selection of a fixed set of slots (n, k fixed), one CUDA graph per
@@ -532,6 +535,10 @@ struct gim_ctx {
   uint32_t queue_cap = 4096;          // GIM_OPT_QUEUE_CAP
   uint64_t big_budget = 16ull << 30;  // GIM_OPT_LARGE_PASS_BYTES
   bool fresh_final = false;           // GIM_OPT_FRESH_FINAL
+  bool compact = false;               // GIM_OPT_COMPACT_FIRST_PICK
+  // Sets holding this vertex keep only their size and counts (compact
+  // collections: gim_imm sets it to its first selection's first pick).
+  uint32_t skip_vertex = gim::kNoSkip;
 
   gim::SelectBuffers sel;
   gim::MultiSelect *msel = nullptr;   // gim_select_seeds / gim_imm: a one-slot batched selection

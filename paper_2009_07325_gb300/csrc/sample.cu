@@ -94,11 +94,12 @@ struct InstView {
   uint32_t rhi;    // high word of the root draw
   uint32_t moff;   // stored member = moff + vertex
   uint32_t idoff;
+  uint32_t skip;   // sets holding this vertex keep only their size (kNoSkip: none)
 };
 
 __device__ __forceinline__ InstView view_of(const InstDesc &d) {
   return InstView{d.n, d.off, d.src, d.thr, d.rthr, d.rw, d.cum, d.members, d.store_cap, d.rr_start, d.rr_len, d.cnt,
-                  d.key, d.j_begin, d.jhi, d.rhi, d.moff, d.idoff};
+                  d.key, d.j_begin, d.jhi, d.rhi, d.moff, d.idoff, d.skip};
 }
 
 // Low word of the rr_id of the set at position j.
@@ -129,31 +130,42 @@ __device__ __forceinline__ void defer(const SampleLaunch &L, uint32_t ii, uint64
 
 // Warp-wide: copies the finished set q[0..size) to instance ii's store and
 // bumps its occurrence counts; clears the set's bitmap bits when bm != null.
-// Defers the set if the store is full.
+// Defers the set if the store is full. A set that holds the instance's
+// skipped vertex is counted but not copied (rr_start = kSkipped).
 __device__ __forceinline__ void commit_warp(const SampleLaunch &L, const InstView &V, uint32_t ii, uint64_t j,
                                             const uint32_t *q, uint32_t size, uint32_t *bm) {
   InstDesc &D = L.inst[ii];
   const uint32_t lane = lane_id();
+  bool skipped = false;
+  if (V.skip != kNoSkip) {
+    if (bm) {
+      skipped = (bm[V.skip >> 5] >> (V.skip & 31u)) & 1u;
+    } else {
+      bool has = false;
+      for (uint32_t i = lane; i < size; i += 32) has |= q[i] == V.skip;
+      skipped = __any_sync(kFullMask, has);
+    }
+    __syncwarp();
+  }
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(&D.store_tail, (unsigned long long)size);
+  if (lane == 0 && !skipped) base = atomicAdd(&D.store_tail, (unsigned long long)size);
   base = __shfl_sync(kFullMask, base, 0);
-  const bool fits = base + size <= V.store_cap;
+  const bool fits = skipped || base + size <= V.store_cap;
+  const bool copy = fits && !skipped;
   uint32_t *members = V.members;
   uint32_t *cnt = V.cnt;
   for (uint32_t i = lane; i < size; i += 32) {
     const uint32_t x = q[i];
-    if (fits) {
-      members[base + i] = V.moff + x;
-      atomicAdd(&cnt[V.moff + x], 1u);
-    }
+    if (copy) members[base + i] = V.moff + x;
+    if (fits) atomicAdd(&cnt[V.moff + x], 1u);
     if (bm) bm[x >> 5] = 0u;   // every set bit of the bitmap belongs to this set
   }
   __syncwarp();
   if (lane == 0) {
     if (fits) {
-      V.rr_start[j] = base;
+      V.rr_start[j] = skipped ? kSkipped : base;
       V.rr_len[j] = size;
-      atomicAdd(&D.members_added, (unsigned long long)size);
+      if (!skipped) atomicAdd(&D.members_added, (unsigned long long)size);
     } else {
       defer(L, ii, j);
     }
@@ -771,14 +783,20 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       __syncthreads();
       continue;
     }
-    if (tid == 0) s_base = atomicAdd(&L.inst[ii].store_tail, (unsigned long long)size);
+    // a set holding the skipped vertex is counted but not copied (its bit,
+    // read before the bitmap is cleared)
+    if (tid == 0) {
+      const bool sk = V.skip != kNoSkip && ((bm[V.skip >> 5] >> (V.skip & 31u)) & 1u);
+      s_base = sk ? kSkipped : atomicAdd(&L.inst[ii].store_tail, (unsigned long long)size);
+    }
     __syncthreads();
     const unsigned long long base = s_base;
-    const bool fits = base + size <= V.store_cap;
+    const bool skipped = base == kSkipped;
+    const bool fits = skipped || base + size <= V.store_cap;
     for (uint32_t i = tid; i < size; i += kBigBlock) {
       const uint32_t x = q[i];
       if (fits) {
-        V.members[base + i] = V.moff + x;
+        if (!skipped) V.members[base + i] = V.moff + x;
         atomicAdd(&V.cnt[V.moff + x], 1u);
       }
       bm[x >> 5] = 0u;
@@ -787,7 +805,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       if (fits) {
         V.rr_start[j] = base;
         V.rr_len[j] = size;
-        atomicAdd(&L.inst[ii].members_added, (unsigned long long)size);
+        if (!skipped) atomicAdd(&L.inst[ii].members_added, (unsigned long long)size);
       } else {
         defer(L, ii, j);
       }
@@ -1096,22 +1114,35 @@ __global__ void __launch_bounds__(32 * kLtMultiWarps) lt_multi_kernel(SampleLaun
     __syncwarp();
     // commit the walks that ended
     const bool commit = active && ended && !overflow;
+    // a walk through the skipped vertex is counted but not copied
+    bool sk = false;
+    {
+      const uint32_t mine = (commit && V.skip != kNoSkip) ? len : 0u;
+      uint32_t top = mine;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(kFullMask, top, o));
+      for (uint32_t i0 = 0; i0 < top; i0 += kLtLanes) {
+        const uint32_t i = i0 + gl;
+        const bool hit = i < mine && path[i] == V.skip;
+        sk |= ((__ballot_sync(kFullMask, hit) >> lead) & 0xFFu) != 0u;
+      }
+    }
     unsigned long long base = 0;
-    if (commit && gl == 0) base = atomicAdd(&L.inst[ii].store_tail, (unsigned long long)len);
+    if (commit && gl == 0) base = sk ? kSkipped : atomicAdd(&L.inst[ii].store_tail, (unsigned long long)len);
     base = __shfl_sync(kFullMask, base, lead);
     if (commit) {
-      const bool fits = base + len <= V.store_cap;
+      const bool fits = sk || base + len <= V.store_cap;
       if (fits)
         for (uint32_t i = gl; i < len; i += kLtLanes) {
           const uint32_t m = V.moff + path[i];
-          V.members[base + i] = m;
+          if (!sk) V.members[base + i] = m;
           atomicAdd(&V.cnt[m], 1u);
         }
       if (gl == 0) {
         if (fits) {
           V.rr_start[j] = base;
           V.rr_len[j] = len;
-          atomicAdd(&L.inst[ii].members_added, (unsigned long long)len);
+          if (!sk) atomicAdd(&L.inst[ii].members_added, (unsigned long long)len);
         } else {
           defer(L, ii, j);
         }
@@ -1147,6 +1178,10 @@ __global__ void uncount_kernel(SampleLaunch L) {
     const InstDesc &D = L.inst[ii];
     const uint64_t b = D.rr_start[j];
     if (b == kNoStart) continue;
+    if (b == kSkipped) {   // its members are not kept: the host empties the collection instead
+      if (lane == 0) atomicOr(&L.ctl->err, kErrUncountSkipped);
+      continue;
+    }
     const uint32_t len = D.rr_len[j];
     for (uint32_t t = lane; t < len; t += 32) atomicSub(&D.cnt[D.members[b + t]], 1u);
   }

@@ -60,6 +60,7 @@ gim_status reset_all(gim_ctx *const *ctxs, uint32_t ni, cudaStream_t s) {
     ctxs[i]->model = -1;
     ctxs[i]->jhi = ctxs[i]->rhi = 0;
     ctxs[i]->rounds = 1;
+    ctxs[i]->skip_vertex = kNoSkip;
     const cudaError_t e = cudaMemsetAsync(ctxs[i]->st.cnt, 0, (uint64_t)ctxs[i]->g.n * 4, s);
     if (e != cudaSuccess) return cuda_err(ctxs[0], e, "autotune reset");
   }

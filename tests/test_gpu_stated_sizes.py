@@ -187,3 +187,45 @@ def test_ic_p001_rmat22_lower_bound_collections_oracle_greedy():
         assert gains.tolist() == og.tolist() and cov == oc, i
         orc.reset()
     ctx.close()
+
+
+def test_ic_p001_rmat22_stated_k100_eps005_compact():
+    """The stated configuration, k = 100 and eps = 0.05 (theta about 1.6e7 RR
+    sets, 4.9 % of them giant, ~2e5 members): run with compact collections
+    (the sets drawn after the first selection that hold its first pick keep
+    only their size). Checked: theta against the oracle's constants and the
+    run's LB; a seeded sample of sets (stored and compact) and the largest
+    stored ones redrawn by the oracle one by one (a compact set: the oracle's
+    set has its size and holds the first seed); the first seed is the
+    argmax of the occurrence counts, lowest id on ties."""
+    g = I.uniform_weights(I.rmat(22, 3), 0.01)
+    k, eps = 100, 0.05
+    c = O.imm_constants(g.n, k, eps, 1.0)
+    ctx = Context(0)
+    ctx.load(g)
+    ctx.set_option(binding.GIM_OPT_COMPACT_FIRST_PICK, 1)
+    t0 = time.perf_counter()
+    r = ctx.imm(GIM_IC, k, eps, 1.0, 7)
+    secs = time.perf_counter() - t0
+    R, Z = ctx.rr_count()
+    assert r["theta"] == math.ceil(c["lambda_star"] / r["lb"]) and R == r["rr_count"] >= r["theta"]
+    cnt = ctx.coverage()
+    u1 = int(r["seeds"][0])
+    assert cnt[u1] == cnt.max() and u1 == int(np.flatnonzero(cnt == cnt.max())[0])
+    orc = O.Oracle(g)
+    rng = np.random.default_rng(2026)
+    ids = sorted(set(rng.choice(R, size=40, replace=False).tolist()) | {0, R - 1})
+    n_compact = 0
+    for j in ids:
+        size, stored = ctx.rr_info(j)
+        want = np.sort(orc.rr_one(GIM_IC, 7, j))
+        assert size == len(want), f"RR set {j} size"
+        if stored:
+            assert np.array_equal(ctx.rr_get(j), want), f"RR set {j} differs"
+        else:
+            n_compact += 1
+            assert u1 in want, f"compact RR set {j} does not hold the first seed"
+    assert n_compact > 0
+    print(f"p=0.01 k={k} eps={eps}: theta={r['theta']} lb={r['lb']:.1f} |R|={R} stored members={Z} "
+          f"seconds={secs:.1f} compact sampled={n_compact}/{len(ids)}")
+    ctx.close()
