@@ -621,15 +621,19 @@ cudaError_t ensure_buf(T *&p, uint64_t &cap, uint64_t need) {
 // The fixed launch sequence that prepares a batched selection: counts (for
 // instances that count a prefix) and the inverted index. The greedy rounds
 // follow as cooperative launches of the greedy kernel (greedy.cu).
+// compact: some instance holds a compact collection (the sequence then
+// includes its three steps; they do nothing for the other instances).
 cudaError_t enqueue_selection(SelDesc *d, uint32_t ni, uint32_t scan_blocks, uint32_t fill_blocks,
-                              uint32_t cnt_blocks, cudaStream_t s) {
+                              uint32_t cnt_blocks, bool compact, cudaStream_t s) {
   const uint32_t ny = std::min<uint32_t>(ni, 65535);
   bsel_clear<<<dim3(64, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_cnt_clear<<<dim3(cnt_blocks, ny), kSelThreads, 0, s>>>(d, ni);
   bsel_count<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
-  bsel_pick<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
-  bsel_detect<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
-  bsel_count_open<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  if (compact) {
+    bsel_pick<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
+    bsel_detect<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+    bsel_count_open<<<fill_blocks, kSelThreads, 0, s>>>(d, ni);
+  }
   bsel_tile_sums<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
   bsel_tile_scan<<<ni, kSelThreads, 0, s>>>(d, ni);
   bsel_apply<<<scan_blocks, kSelThreads, 0, s>>>(d, ni);
@@ -698,16 +702,18 @@ struct MultiSelect::Impl {
   std::vector<uint64_t> seed_off;
   std::vector<uint32_t> k_cfg;
   uint32_t ni = 0, scan_blocks = 0, fill_blocks = 0, cnt_blocks = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};   // without and with the compact-collection steps
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
   // greedy rounds: block groups, and the waves of instances that share one cooperative launch
   std::vector<GreedyDesc> gh;
   GreedyDesc *gd = nullptr;
   unsigned int *sync = nullptr;          // ni group barriers, then the error flag
   std::vector<uint32_t> wave_first, wave_grid;
   ~Impl() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
+    for (int v = 0; v < 2; ++v) {
+      if (exec[v]) cudaGraphExecDestroy(exec[v]);
+      if (graph[v]) cudaGraphDestroy(graph[v]);
+    }
     if (gd) cudaFree(gd);
     if (sync) cudaFree(sync);
     if (d) cudaFree(d);
@@ -921,20 +927,23 @@ gim_status MultiSelect::run(gim_ctx *ctx, const std::vector<SelInput> &in, cudaS
   CU(cudaMemcpyAsync(B.d, B.h.data(), B.ni * sizeof(SelDesc), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(B.gd, B.gh.data(), B.ni * sizeof(GreedyDesc), cudaMemcpyHostToDevice, s));
   CU(cudaMemsetAsync(B.sync + B.ni, 0, sizeof(unsigned int), s));
-  if (!B.exec) {
+  bool any_compact = false;
+  for (uint32_t i = 0; i < B.ni; ++i) any_compact = any_compact || B.h[i].compact;
+  const int gv = any_compact ? 1 : 0;
+  if (!B.exec[gv]) {
     // the launch sequence is fixed for these slots; the round's inputs live in B.d
     CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t ce = enqueue_selection(B.d, B.ni, B.scan_blocks, B.fill_blocks, B.cnt_blocks, s);
+    const cudaError_t ce = enqueue_selection(B.d, B.ni, B.scan_blocks, B.fill_blocks, B.cnt_blocks, any_compact, s);
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s, &g);
     if (ce != cudaSuccess) return cuda_err(ctx, ce, "selection capture");
     if (ee != cudaSuccess) return cuda_err(ctx, ee, "selection capture");
-    B.graph = g;
-    CU(cudaGraphInstantiate(&B.exec, B.graph, 0));
+    B.graph[gv] = g;
+    CU(cudaGraphInstantiate(&B.exec[gv], B.graph[gv], 0));
   }
   CU(cudaEventRecord(ctx->ev[8], s));
-  CU(cudaGraphLaunch(B.exec, s));
-  ctx->launches += 14;
+  CU(cudaGraphLaunch(B.exec[gv], s));
+  ctx->launches += any_compact ? 14 : 11;
   for (size_t w = 0; w < B.wave_first.size(); ++w) {
     const uint32_t first = B.wave_first[w];
     const uint32_t count = (w + 1 < B.wave_first.size() ? B.wave_first[w + 1] : B.ni) - first;
