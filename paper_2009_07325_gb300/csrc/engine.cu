@@ -149,6 +149,7 @@ void shared_free(DeviceShared &D) {
   dfree(D.d_defslot);
   D.def_cap = 0;
   dfree(D.lt_ovf);
+  dfree(D.ic_ovf);
   dfree(D.d_ovf_next);
   dfree(D.d_ctl);
   if (D.h_ctl) cudaFreeHost(D.h_ctl);
@@ -172,6 +173,7 @@ gim_status shared_acquire(gim_ctx *ctx) {
     if (e == cudaSuccess) e = cudaMemset(D.cs.epoch, 0, (uint64_t)workers * 4);
     if (e == cudaSuccess) e = cudaMalloc(&D.d_ctl, sizeof(SampleCtl));
     if (e == cudaSuccess) e = cudaMalloc(&D.lt_ovf, (uint64_t)kLtOvfSlots * kLtGroupPath * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&D.ic_ovf, (uint64_t)kIcOvfSlots * kIcOvfStride * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&D.d_ovf_next, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&D.h_ctl, sizeof(SampleCtl));
     if (e != cudaSuccess) {
@@ -328,6 +330,8 @@ gim_status run_one(gim_ctx *ctx, DeviceShared &D, int model, std::vector<SampleJ
   L.lt_ovf = D.lt_ovf;
   L.lt_ovf_next = D.d_ovf_next;
   L.lt_ovf_cap = kLtOvfSlots;
+  L.ic_ovf = D.ic_ovf;
+  L.ic_ovf_cap = kIcOvfSlots;
   if (used) *used = L;
   CU(cudaEventRecord(ctx->ev[6], s));
   cudaError_t e;
@@ -435,7 +439,7 @@ gim_status sample_jobs(std::vector<SampleJobH> &jobs, cudaStream_t s) {
     };
     unsigned long long *list_a = D.d_def, *list_b = D.d_def + D.def_cap / 2;
     uint32_t *slot_a = D.d_defslot, *slot_b = D.d_defslot + D.def_cap / 2;
-    CU(cudaMemsetAsync(D.d_ovf_next, 0, sizeof(unsigned int), s));   // saved LT paths of this call
+    CU(cudaMemsetAsync(D.d_ovf_next, 0, sizeof(unsigned int), s));   // saved LT paths / IC states of this call
     Pass P{false, total, nullptr, list_a, nullptr, slot_a};
     if ((st = run_one(ctx, D, model, grp, P, s, &L0)) != GIM_OK) return rollback(), st;
     uint64_t pending = D.h_ctl->n_deferred;

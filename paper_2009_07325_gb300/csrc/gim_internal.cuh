@@ -224,14 +224,21 @@ struct SampleLaunch {
   const uint32_t *item_slots;        // nullable
   uint32_t *deferred_slots;          // nullable
   uint32_t *lt_ovf;                  // lt_ovf_cap slots of kLtGroupPath vertices
-  unsigned int *lt_ovf_next;         // slots handed out in this sampling call
+  unsigned int *lt_ovf_next;         // slots handed out in this sampling call (LT or IC: one model per launch)
   uint32_t lt_ovf_cap;
+  // IC sets the warp-per-set pass hands on past their budget keep their
+  // state in a slot of kIcOvfStride words (members so far, rows expanded,
+  // then the members), so the block-per-set pass continues them
+  uint32_t *ic_ovf;                  // ic_ovf_cap slots
+  uint32_t ic_ovf_cap;
 };
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr uint32_t kLtGroupPath = 384;     // LT common pass: path entries per walk (shared memory)
 constexpr uint32_t kLtOvfSlots = 16384;     // LT walks continued from a saved path per sampling call
 
 constexpr uint32_t kQueueCap = 4096;        // common pass: members per set before it is deferred
+constexpr uint32_t kIcOvfStride = kQueueCap + 2;   // an IC overflow slot: tail, head, then the queue
+constexpr uint32_t kIcOvfSlots = 65536;       // IC sets continued from a saved state per sampling pass
 constexpr uint32_t kHashBits = 13;
 constexpr uint32_t kHashSlots = 1u << kHashBits;   // common pass: visited hash slots per worker
 
@@ -381,6 +388,7 @@ struct DeviceShared {
   uint32_t *d_defslot = nullptr;       // their overflow slots (same layout)
   uint64_t def_cap = 0;
   uint32_t *lt_ovf = nullptr;          // kLtOvfSlots saved LT paths
+  uint32_t *ic_ovf = nullptr;          // kIcOvfSlots saved IC states
   unsigned int *d_ovf_next = nullptr;
   SampleCtl *d_ctl = nullptr;
   SampleCtl *h_ctl = nullptr;          // pinned

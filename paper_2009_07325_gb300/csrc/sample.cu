@@ -529,11 +529,12 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
       ht[(root * 0x9E3779B1u) >> (32 - kHashBits)] = ((unsigned long long)epoch << 32) | root;
     }
     uint32_t head = 0, tail = 1, scanned = 0;
-    bool overflow = false;
+    bool overflow = false, budget_stop = false;
     while (head < tail && !overflow) {
       __syncwarp();
       if (scanned > L.group_budget) {          // a heavy set: hand it to the large-set pass
         overflow = true;
+        budget_stop = true;
         break;
       }
       const uint32_t nb = tail - head < 32u ? tail - head : 32u;
@@ -579,7 +580,27 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
       common_flush(src, cand, ncand, ht, epoch, q, tail, overflow, qcap);
     }
     if (overflow) {
-      if (lane == 0) defer(L, ii, j);
+      // Past the budget the set stops between frontier batches: q[0, tail) is
+      // its visited set and the rows of q[0, head) are expanded with every live
+      // edge resolved, so it is saved for the block pass to continue (RR set j
+      // does not depend on who expands which row when). A set that outgrew
+      // the queue lost vertices and starts over.
+      uint32_t slot = kNoSlot;
+      if (budget_stop && L.ic_ovf) {
+        if (lane == 0) slot = atomicAdd(L.lt_ovf_next, 1u);
+        slot = __shfl_sync(kFullMask, slot, 0);
+        if (slot < L.ic_ovf_cap) {
+          uint32_t *sv = L.ic_ovf + (uint64_t)slot * kIcOvfStride;
+          for (uint32_t i = lane; i < tail; i += 32) sv[2 + i] = q[i];
+          if (lane == 0) {
+            sv[0] = tail;
+            sv[1] = head;
+          }
+        } else {
+          slot = kNoSlot;
+        }
+      }
+      if (lane == 0) defer(L, ii, j, slot);
       continue;
     }
     commit_warp(L, V, ii, j, q, tail, nullptr);
@@ -639,7 +660,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
   __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
   __shared__ uint32_t w_tot[kBigWarps];
   __shared__ unsigned long long s_item, s_base;
-  __shared__ uint32_t s_tail, s_next;
+  __shared__ uint32_t s_tail, s_next, s_head, s_slot;
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t *cand = cand_all[warp];
   uint32_t *pe = pe_all[warp], *pt = pt_all[warp];
@@ -656,18 +677,38 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       const unsigned long long it = atomicAdd(&L.ctl->next, 1ull);
       s_item = it;
       if (it < L.total_items) {
-        uint32_t i0;
-        uint64_t j0;
-        const InstView V0 = item_view<kOne>(L, one, it, i0, j0);
-        const uint32_t root = draw_root(V0.key, id_lo(V0, j0), V0.rhi, V0.n);
-        q[0] = root;
-        bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
-        s_tail = 1;
+        const uint32_t slot = L.item_slots && L.ic_ovf ? L.item_slots[it] : kNoSlot;
+        if (slot < L.ic_ovf_cap) {   // a set the warp pass saved: continue it
+          const uint32_t *sv = L.ic_ovf + (uint64_t)slot * kIcOvfStride;
+          s_slot = slot;
+          s_tail = sv[0];
+          s_head = sv[1];
+        } else {
+          uint32_t i0;
+          uint64_t j0;
+          const InstView V0 = item_view<kOne>(L, one, it, i0, j0);
+          const uint32_t root = draw_root(V0.key, id_lo(V0, j0), V0.rhi, V0.n);
+          q[0] = root;
+          bm[root >> 5] = 1u << (root & 31u);   // the slot's bitmap is all zero here
+          s_slot = kNoSlot;
+          s_tail = 1;
+          s_head = 0;
+        }
       }
     }
     __syncthreads();
     const unsigned long long item = s_item;
     if (item >= L.total_items) break;
+    if (s_slot != kNoSlot) {   // the saved visited set: queue entries and bitmap bits
+      const uint32_t *sv = L.ic_ovf + (uint64_t)s_slot * kIcOvfStride + 2;
+      const uint32_t t = s_tail;
+      for (uint32_t i = tid; i < t; i += kBigBlock) {
+        const uint32_t v = sv[i];
+        q[i] = v;
+        atomicOr(&bm[v >> 5], 1u << (v & 31u));
+      }
+      __syncthreads();
+    }
     uint32_t ii;
     uint64_t j;
     const InstView V = item_view<kOne>(L, one, item, ii, j);
@@ -679,7 +720,7 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
     const CoinKey ck = coin_key(id_lo(V, j), V.jhi, key);
     uint32_t ncand = 0, npend = 0;             // this warp's buffered live edges, pending screened edges
     auto flush = [&]() { block_flush(src, cand, ncand, bm, q, qcap, &s_tail); };
-    uint32_t head = 0;                         // frontier vertices expanded (the same in every thread)
+    uint32_t head = s_head;                    // frontier vertices expanded (the same in every thread)
     for (;;) {
       const uint32_t tail = s_tail;
       if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
