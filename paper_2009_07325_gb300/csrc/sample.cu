@@ -611,13 +611,16 @@ __global__ void __launch_bounds__(256, 4) ic_common_kernel(SampleLaunch L, Commo
 // ---------------------------------------------------------------------------
 // IC large-set pass: one block of kBigBlock threads per RR set.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kRowsPerThread = 1;       // frontier rows each thread loads per block step
-constexpr uint32_t kBatch = kBigBlock * kRowsPerThread;   // frontier vertices per block step, at most
+constexpr uint32_t kBatch = kBigBlock;        // frontier vertices per block step, at most (one row per thread)
 constexpr uint32_t kBigWarps = kBigBlock / 32;
 constexpr uint32_t kBigCand = 128 * kGPL;    // per-warp candidate buffer: one warp step's live edges at most
 // A chunk is L.chunk_groups groups of 4 in-edges, or half as many
 // super-groups of 16 in a screened row; a chunk's last warp step may be
-// partial (its groups past the chunk are masked off).
+// partial (its groups past the chunk are masked off). The chunks of a batch
+// are handed out longest first: every chunk of the rows that need several
+// (found by a search over their few prefix entries), then the one-chunk rows
+// in queue order (found by a direct index), so the short ones fill the gaps
+// at the end of a batch.
 
 // Resolves a warp's buffered live edges: a source not yet in the set joins
 // the queue. Past the queue's capacity the vertex is not kept (its bit is
@@ -657,8 +660,9 @@ template <bool kOne>
 __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(SampleLaunch L, BigScratch bs, InstDesc one) {
   __shared__ uint32_t cand_all[kBigWarps][kBigCand];
   __shared__ uint32_t pe_all[kBigWarps][kPend], pt_all[kBigWarps][kPend];
-  __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch], b_pre[kBatch + 1];
-  __shared__ uint32_t w_tot[kBigWarps];
+  __shared__ uint32_t b_s[kBatch], b_e[kBatch], b_rt[kBatch];
+  __shared__ uint32_t m_row[kBatch], m_pre[kBatch + 1], s_row[kBatch];   // multi-chunk rows, one-chunk rows
+  __shared__ uint32_t w_tot[kBigWarps][2];
   __shared__ unsigned long long s_item, s_base;
   __shared__ uint32_t s_tail, s_next, s_head, s_slot;
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -725,70 +729,82 @@ __global__ void __launch_bounds__(kBigBlock, kBigBlocksPerSM) ic_block_kernel(Sa
       const uint32_t tail = s_tail;
       if (head >= tail || tail > qcap) break;   // done, or the queue overflowed
       const uint32_t nb = tail - head < batch ? tail - head : batch;
-      uint32_t nch[kRowsPerThread], mine = 0;  // chunks of this thread's frontier rows
-#pragma unroll
-      for (uint32_t r = 0; r < kRowsPerThread; ++r) {
-        const uint32_t b = tid * kRowsPerThread + r;
-        nch[r] = 0;
-        if (b < nb) {
-          const uint32_t v = q[head + b];
-          const uint32_t s = off[v], e = off[v + 1], rt = rthr[v];
-          b_s[b] = s;
-          b_e[b] = e;
-          b_rt[b] = rt;
-          // a chunk is cgroups groups of 4 in-edges, or cgroups / 2 super-groups of 16
-          const bool sc = screened(rt);
-          const uint32_t sh = sc ? 4u : 2u, cg = sc ? cgroups >> 1 : cgroups;
-          nch[r] = (e > s && rt != 0u) ? (((e - 1) >> sh) - (s >> sh) + cg) / cg : 0u;
-        }
-        mine += nch[r];
+      uint32_t nch = 0;                        // chunks of this thread's frontier row
+      if (tid < nb) {
+        const uint32_t v = q[head + tid];
+        const uint32_t s = off[v], e = off[v + 1], rt = rthr[v];
+        b_s[tid] = s;
+        b_e[tid] = e;
+        b_rt[tid] = rt;
+        // a chunk is cgroups groups of 4 in-edges, or cgroups / 2 super-groups of 16
+        const bool sc = screened(rt);
+        const uint32_t sh = sc ? 4u : 2u, cg = sc ? cgroups >> 1 : cgroups;
+        nch = (e > s && rt != 0u) ? (((e - 1) >> sh) - (s >> sh) + cg) / cg : 0u;
       }
-      // block-wide exclusive prefix of the chunk counts (rows >= nb hold 0)
-      uint32_t wsum;
-      const uint32_t wex = warp_excl(mine, wsum);
-      if (lane == 0) w_tot[warp] = wsum;
+      // block-wide exclusive prefixes: one-chunk rows and multi-chunk rows
+      // (packed, 16 bits each: at most kBatch of either), chunks of the latter
+      uint32_t wsum_r, wsum_c;
+      const uint32_t wex_r = warp_excl((nch == 1u ? 1u : 0u) | (nch > 1u ? 0x10000u : 0u), wsum_r);
+      const uint32_t wex_c = warp_excl(nch > 1u ? nch : 0u, wsum_c);
+      if (lane == 0) {
+        w_tot[warp][0] = wsum_r;
+        w_tot[warp][1] = wsum_c;
+      }
       if (tid == 0) s_next = 0;
       __syncthreads();
-      uint32_t before = 0, all = 0;
+      uint32_t before_r = 0, before_c = 0, all_r = 0, all_c = 0;
       for (uint32_t w = 0; w < kBigWarps; ++w) {
-        if (w < warp) before += w_tot[w];
-        all += w_tot[w];
+        if (w < warp) {
+          before_r += w_tot[w][0];
+          before_c += w_tot[w][1];
+        }
+        all_r += w_tot[w][0];
+        all_c += w_tot[w][1];
       }
-      uint32_t run = before + wex;
-#pragma unroll
-      for (uint32_t r = 0; r < kRowsPerThread; ++r) {
-        const uint32_t b = tid * kRowsPerThread + r;
-        if (b < nb) b_pre[b] = run;
-        run += nch[r];
+      const uint32_t n_multi = all_r >> 16, n_one = all_r & 0xFFFFu;
+      if (nch == 1u) {
+        s_row[(before_r + wex_r) & 0xFFFFu] = tid;
+      } else if (nch > 1u) {
+        const uint32_t m = (before_r + wex_r) >> 16;
+        m_row[m] = tid;
+        m_pre[m] = before_c + wex_c;
       }
-      if (tid == 0) b_pre[nb] = all;
+      if (tid == 0) m_pre[n_multi] = all_c;
       __syncthreads();
-      const uint32_t nchunks = b_pre[nb];
+      const uint32_t nchunks = all_c + n_one;
       for (;;) {
         uint32_t c = 0;
         if (lane == 0) c = atomicAdd(&s_next, 1u);
         c = __shfl_sync(kFullMask, c, 0);
         if (c >= nchunks) break;
-        uint32_t lo = 0, hi = nb - 1;          // vertex b with b_pre[b] <= c < b_pre[b + 1]
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (b_pre[mid] <= c)
-            lo = mid;
-          else
-            hi = mid - 1;
+        uint32_t row, k;                       // the chunk's row and its index within the row
+        if (c < all_c) {
+          uint32_t lo = 0, hi = n_multi - 1;   // multi-chunk row m with m_pre[m] <= c < m_pre[m + 1]
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (m_pre[mid] <= c)
+              lo = mid;
+            else
+              hi = mid - 1;
+          }
+          row = m_row[lo];
+          k = c - m_pre[lo];
+        } else {
+          row = s_row[c - all_c];
+          k = 0;
         }
-        const uint32_t s = b_s[lo], e = b_e[lo], rt = b_rt[lo], rl = lim(rt);
+        const uint32_t s = b_s[row], e = b_e[row], rt = b_rt[row], rl = lim(rt);
         if (screened(rt)) {
           const uint32_t g0 = s >> 4, g1 = (e - 1) >> 4;
           const uint32_t csg = cgroups >> 1;
-          const uint32_t c0 = g0 + (c - b_pre[lo]) * csg;
+          const uint32_t c0 = g0 + k * csg;
           const uint32_t c1 = c0 + csg - 1 < g1 ? c0 + csg - 1 : g1;
           for (uint32_t base = c0; base <= c1; base += kStepSG)
             step_screened<kSGPL>(base, c1, s, e, rt, ck, pe, pt, npend, cand, ncand, kBigCand, flush);
           continue;
         }
         const uint32_t g0 = s >> 2, g1 = (e - 1) >> 2;
-        const uint32_t c0 = g0 + (c - b_pre[lo]) * cgroups;
+        const uint32_t c0 = g0 + k * cgroups;
         const uint32_t c1 = c0 + cgroups - 1 < g1 ? c0 + cgroups - 1 : g1;
         for (uint32_t base = c0; base <= c1; base += kStepGroups) {
           uint32_t lv[kGPL];
