@@ -6,8 +6,10 @@ Barabasi-Albert graphs of 10^6 vertices (r = 2 and 32, k = 50, eps = 0.05).
 All with l = 1 and Philox seed 7, after the same schedule autotuning the benchmark
 runs. The oracle cannot redraw a million RR sets in a test's time, so:
 
-* RR sets: a seeded sample of rr_ids plus the largest sets, each redrawn by
-  the oracle one by one and compared as sorted vertex lists;
+* RR sets: every set of a prefix of rr_ids (tens of thousands, drawn by the
+  oracle on all host cores), plus a seeded sample of rr_ids over the whole
+  collection and the largest sets, each redrawn by the oracle one by one, all
+  compared as sorted vertex lists;
 * occurrence counts: equal to the member histogram of the exported store;
 * IMM: the oracle runs Alg. 2 and Alg. 1 over the GPU's collection (each
   "sample until |R| >= t" served by its first t sets), which must give the
@@ -36,6 +38,26 @@ def rmat22_wc():
     return I.wc_weights(I.rmat(22, 3))
 
 
+def _keyed(off, mem, count):
+    """The first `count` sets of a collection as sorted (set << 32 | vertex) keys."""
+    off = np.asarray(off, dtype=np.int64)
+    end = int(off[count])
+    sets = np.repeat(np.arange(count, dtype=np.uint64), np.diff(off[:count + 1]))
+    return np.sort((sets << np.uint64(32)) | np.asarray(mem[:end], dtype=np.uint64))
+
+
+def _prefix_matches(g, model, seed, off, mem, count):
+    """Every one of the first `count` RR sets equals the oracle's (a sampling fault
+    that spares a random sample still shows up here)."""
+    count = min(count, len(off) - 1)
+    o = O.Oracle(g)
+    o.sample(model, seed, count, max(1, O.max_threads()))
+    ooff, omem = o.export()
+    assert len(ooff) - 1 == count
+    assert np.array_equal(_keyed(off, mem, count), _keyed(ooff, omem, count)), "a prefix RR set differs"
+    o.close()
+
+
 def _sampled_sets_match(ctx, orc, model, seed, off, mem, n_sample=256):
     R = len(off) - 1
     rng = np.random.default_rng(12345)
@@ -61,6 +83,7 @@ def test_imm_rmat22_full_size(rmat22_wc, model, k, eps):
     assert len(off) - 1 == r["rr_count"] >= r["theta"]
     orc = O.Oracle(g)
     _sampled_sets_match(ctx, orc, model, 7, off, mem)
+    _prefix_matches(g, model, 7, off, mem, 50000)
     orc.load_csr(off, mem)
     o = orc.imm_replay(k, eps, 1.0)
     assert r["seeds"].tolist() == o["seeds"].tolist()
@@ -114,6 +137,7 @@ def test_imm_barabasi_albert_full_size(r):
     assert len(off) - 1 == res["rr_count"] >= res["theta"]
     orc = O.Oracle(g)
     _sampled_sets_match(ctx, orc, GIM_IC, 7, off, mem)
+    _prefix_matches(g, GIM_IC, 7, off, mem, 20000)
     orc.load_csr(off, mem)
     o = orc.imm_replay(k, eps, 1.0)
     assert res["seeds"].tolist() == o["seeds"].tolist()

@@ -60,6 +60,22 @@ def _sampled_sets_match(orc, model, seed, off, mem, n_sample=256, rng_seed=12345
         assert np.array_equal(got, want), f"RR set {j} differs"
 
 
+def _prefix_matches(g, model, seed, off, mem, count):
+    """Every one of the first `count` RR sets equals the oracle's, drawn on all host cores."""
+    count = min(count, len(off) - 1)
+    o = O.Oracle(g)
+    o.sample(model, seed, count, THREADS)
+    ooff, omem = o.export()
+
+    def keyed(a, b):
+        a = np.asarray(a, dtype=np.int64)
+        sets = np.repeat(np.arange(count, dtype=np.uint64), np.diff(a[:count + 1]))
+        return np.sort((sets << np.uint64(32)) | np.asarray(b[:int(a[count])], dtype=np.uint64))
+
+    assert np.array_equal(keyed(off, mem), keyed(ooff, omem)), "a prefix RR set differs"
+    o.close()
+
+
 def test_imm_rmat20_ic_wc_full_size():
     g = I.wc_weights(I.rmat(20, 2))
     k, eps = 50, 0.1
@@ -72,6 +88,7 @@ def test_imm_rmat20_ic_wc_full_size():
     assert np.array_equal(ctx.coverage(), np.bincount(mem, minlength=g.n).astype(np.uint32))
     orc = O.Oracle(g)
     _sampled_sets_match(orc, GIM_IC, 7, off, mem)
+    _prefix_matches(g, GIM_IC, 7, off, mem, 100000)
     orc.load_csr(off, mem)
     o = orc.imm_replay(k, eps, 1.0)
     assert r["seeds"].tolist() == o["seeds"].tolist()
