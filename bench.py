@@ -376,12 +376,14 @@ def measured_peaks():
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per unit from the committed ncu summary, if the kernel source is unchanged."""
+    """DRAM bytes per unit from the committed ncu summary, if the kernel source is unchanged
+    (the key hashes sample.cu followed by gim_internal.cuh, which holds the launch shapes)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    src = os.path.join(ROOT, "paper_2009_07325_gb300", "csrc", "sample.cu")
+    csrc = os.path.join(ROOT, "paper_2009_07325_gb300", "csrc")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    blob = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("sample.cu", "gim_internal.cuh"))
+    h = hashlib.sha256(blob).hexdigest()[:16]
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == h:

@@ -339,7 +339,9 @@ typedef enum {
      0 (default): reuse. Values other than 0 and 1 are rejected. */
   GIM_OPT_FRESH_FINAL = 2,
   /* Frontier vertices the block-per-set IC pass expands per block step (a
-     level-synchronous batch): 32 .. 256, a multiple of 32. Default 256. */
+     level-synchronous batch): 32 .. 256, a multiple of 32; values above the
+     pass's block size (128 threads, one frontier row each) act as 128.
+     Default 128. */
   GIM_OPT_FRONTIER_BATCH = 3,
   /* In-edge groups (4 in-edges) per work chunk of the block-per-set IC
      pass: 64 .. 4096, a multiple of 64. A row with p <= 2^-8 is cut into
@@ -377,7 +379,7 @@ gim_status gim_get_option(gim_ctx *ctx, gim_option opt, uint64_t *value);
 
 /*
  * Autotuner: picks the sampling schedule of a workload - GIM_OPT_GROUP_BUDGET
- * (how long one warp keeps an RR set before a 256-thread block takes it
+ * (how long one warp keeps an RR set before a 128-thread block takes it
  * over, i.e. warps per RR set for heavy sets), then GIM_OPT_CHUNK_GROUPS
  * (the block pass's work chunk), GIM_OPT_FRONTIER_BATCH (its frontier batch)
  * and GIM_OPT_QUEUE_CAP (the warp pass's frontier buffer), one knob at a time

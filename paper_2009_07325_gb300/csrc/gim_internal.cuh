@@ -215,7 +215,7 @@ struct SampleLaunch {
   SampleCtl *ctl;
   uint32_t group_budget;             // common pass: edge groups (4 in-edges) a set may scan
   uint32_t queue_cap;                // common pass: members a set may reach (<= kQueueCap)
-  uint32_t batch;                    // block pass: frontier vertices per block step (<= 256)
+  uint32_t batch;                    // block pass: frontier vertices per block step (<= kBigBlock)
   uint32_t chunk_groups;             // block pass: groups per chunk (a multiple of 64)
   // LT walks that outgrow the common pass's path keep it in an overflow slot
   // (kLtGroupPath entries) so that the large pass continues them instead of
@@ -252,7 +252,7 @@ struct CommonScratch {
 
 // Scratch of the large-set passes: per slot an n-bit visited bitmap (all zero
 // between sets) and a queue: min(n, kSlotQueue) entries in the first pass,
-// n entries in later ones. IC uses one 256-thread block per slot,
+// n entries in later ones. IC uses one kBigBlock-thread block per slot,
 // LT one warp per slot.
 struct BigScratch {
   uint32_t *bitmap = nullptr;
@@ -264,8 +264,11 @@ struct BigScratch {
 };
 constexpr uint32_t kSlotQueue = 1u << 20;   // queue entries per slot in the first large-set pass
 
-constexpr int kBigBlock = 256;
-constexpr int kBigBlocksPerSM = 8;   // block-per-set pass: blocks (slots) per SM, 32 registers per thread
+// Four warps per heavy set and 16 sets per SM: a heavy set's levels are short
+// (critical branching), so fewer warps per set wait less at its barriers
+// (128 threads: 36.8-37.0 ms per headline IMM; 256: 38.0-38.3; 64: 40.5-40.6)
+constexpr int kBigBlock = 128;
+constexpr int kBigBlocksPerSM = 16;   // block-per-set pass: blocks (slots) per SM, 32 registers per thread
 
 // Host launchers (sample.cu).
 // `one` (nullable): the launch's only instance, passed by value so that the
@@ -538,7 +541,7 @@ struct gim_ctx {
 
   bool shared_held = false;       // holds a reference on the device's shared scratch
   uint32_t group_budget = 1u << 14;   // GIM_OPT_GROUP_BUDGET
-  uint32_t frontier_batch = 256;      // GIM_OPT_FRONTIER_BATCH
+  uint32_t frontier_batch = 128;      // GIM_OPT_FRONTIER_BATCH
   uint32_t chunk_groups = 512;        // GIM_OPT_CHUNK_GROUPS
   uint32_t queue_cap = 4096;          // GIM_OPT_QUEUE_CAP
   uint64_t big_budget = 16ull << 30;  // GIM_OPT_LARGE_PASS_BYTES

@@ -28,12 +28,13 @@
 //   each vertex is expanded once). The hash set is stamped with a per-set
 //   epoch, so it is never cleared. A set that outgrows the queue or scans
 //   more than its edge budget is abandoned and deferred.
-// IC, large-set pass: one 256-thread block per deferred set, with an n-bit
-//   visited bitmap and a queue. Each batch of up to 256 frontier
-//   vertices is cut into chunks of at most 2048 in-edges (512 Philox calls),
-//   or 4096 in a super-group row (256 calls), that the block's
-//   warps take from a shared counter, so the heavy tail of huge RR sets is
-//   spread over 8 warps. Only __syncthreads barriers are used.
+// IC, large-set pass: one 128-thread block per deferred set (16 per SM),
+//   with an n-bit visited bitmap and a queue. Each batch of up to 128
+//   frontier vertices is cut into chunks of at most 2048 in-edges (512
+//   Philox calls), or 4096 in a super-group row (256 calls), that the
+//   block's warps take from a shared counter, longest first, so the heavy
+//   tail of huge RR sets is spread over 4 warps. Only __syncthreads
+//   barriers are used.
 // LT: the reverse walk of Sec. III-G (four walks per warp in the common pass, see
 //   lt_multi_kernel; one warp per walk in the large pass): one draw per step,
 //   the chosen in-edge found by a 33-way warp search over the row's sorted

@@ -1,7 +1,7 @@
 // Autotuner of the sampling schedule (see gim_autotune in gim.h).
 //
 // The knobs: the common IC pass's edge budget (how many in-edge groups one
-// warp scans for an RR set before a 256-thread block takes the set over)
+// warp scans for an RR set before a block of the block pass takes it over)
 // and its frontier buffer (members a set may reach on one warp), and the
 // block pass's work chunk and frontier batch. A small budget or buffer
 // sends heavy sets to the block pass early, which bounds the tail of a
@@ -103,9 +103,9 @@ gim_status autotune(gim_ctx *const *ctxs, uint32_t ni, const gim_imm_params *par
     };
     static const uint32_t kBudget[] = {1u << 12, 1u << 14, 1u << 16, 1u << 18, 1u << 30};
     static const uint32_t kChunk[] = {256, 512, 1024, 2048};
-    static const uint32_t kBatchC[] = {64, 128, 256};
+    static const uint32_t kBatchC[] = {32, 64, 128};
     static const uint32_t kQueue[] = {1024, 2048, 4096};
-    best = Schedule{1u << 14, 512, 256, kQueueCap};
+    best = Schedule{1u << 14, 512, 128, kQueueCap};
     double best_ms = -1.0;
     auto sweep = [&](uint32_t Schedule::*knob, const uint32_t *cand, size_t nc) -> gim_status {
       for (size_t c = 0; c < nc; ++c) {

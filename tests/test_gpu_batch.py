@@ -132,7 +132,7 @@ def test_autotune_picks_a_candidate_and_caches_it():
     assert b1 in (1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 30) and m1 and b1 == b2 and not m2
     assert all(c.get_option(binding.GIM_OPT_GROUP_BUDGET) == b1 and c.rr_count() == (0, 0) for c in cs)
     sched = cs[0].schedule()
-    assert sched["chunk_groups"] in (256, 512, 1024, 2048) and sched["frontier_batch"] in (64, 128, 256)
+    assert sched["chunk_groups"] in (256, 512, 1024, 2048) and sched["frontier_batch"] in (32, 64, 128)
     assert sched["queue_cap"] in (1024, 2048, 4096) and all(c.schedule() == sched for c in cs)
     r = binding.batch_imm(cs, params)
     for c, p, x in zip(cs, params, r):
