@@ -266,7 +266,8 @@ constexpr uint32_t kSlotQueue = 1u << 20;   // queue entries per slot in the fir
 
 // Four warps per heavy set and 16 sets per SM: a heavy set's levels are short
 // (critical branching), so fewer warps per set wait less at its barriers
-// (128 threads: 36.8-37.0 ms per headline IMM; 256: 38.0-38.3; 64: 40.5-40.6)
+// (128 threads: 36.8-37.0 ms per headline IMM; 192 x 10: 37.0; 256 x 8: 38.0-38.3;
+// 96 x 21: 37.8; 64 x 32: 40.5-40.6)
 constexpr int kBigBlock = 128;
 constexpr int kBigBlocksPerSM = 16;   // block-per-set pass: blocks (slots) per SM, 32 registers per thread
 
